@@ -1,0 +1,182 @@
+"""Pins for the oracle's Algorithm 3 (dimension-incremental sparse FFT)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lattice, philox, sfft
+
+
+def _run(sig, p, seed, dft="fft"):
+    return sfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"],
+                     seed=seed, dft=dft)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_planted_exact_recovery_tiny(seed):
+    """Noiseless planted polynomial: the detected set is the support and the
+    coefficients are exact up to rounding (Table 5.1 reports 2e-16..5e-16)."""
+    sig, p = W.workload("tiny_d3", seed)
+    res = _run(sig, p, seed)
+    np.testing.assert_array_equal(res.freqs, sig.freqs.astype(np.int64))
+    assert np.max(np.abs(res.coeffs - sig.coeffs) / np.abs(sig.coeffs)) < 1e-13
+
+
+def test_direct_and_fft_tiers_agree():
+    sig, p = W.workload("tiny_d3", 4)
+    a = _run(sig, p, 4, "direct")
+    b = _run(sig, p, 4, "fft")
+    np.testing.assert_array_equal(a.freqs, b.freqs)
+    np.testing.assert_allclose(a.coeffs, b.coeffs, rtol=1e-12, atol=0)
+    assert a.samples == b.samples
+
+
+def test_line_coefficients_projection_identity():
+    """Eq. 4.2 with the 1/K_t factor: the length-K_t DFT of one line equals
+    sum_{h: h_t = k} c_h exp(2 pi i h_(not t).x')."""
+    sig = W.planted_signal(4, 5, 40, seed=11, model="u1_10")
+    K = 2 * sig.N + 1
+    x = philox.uniform(3, philox.ANCHOR_LINE, 2, np.arange(4, dtype=np.uint64), 0, 0)
+    for t in (1, 2, 4):
+        for dft in ("direct", "fft"):
+            y = sfft.sample_line(sig, t, x, K, dft)
+            got = sfft.line_coefficients(y, sig.N)
+            want = np.zeros(K, dtype=complex)
+            for h, c in zip(sig.freqs.astype(np.int64), sig.coeffs):
+                other = np.delete(np.arange(4), t - 1)
+                want[h[t - 1] + sig.N] += c * np.exp(2j * np.pi * np.dot(h[other], x[other]))
+            np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+def test_select_ties_threshold_and_eligibility():
+    p = np.array([3, 1j, -3, 2, 0.5, 3j, 0], dtype=complex)
+    sel = sfft.select(p, 2, 0.0, "abs")
+    # keys 9,1,9,4,.25,9,0 -> the two largest 9's with the smaller ids
+    np.testing.assert_array_equal(sel.chosen, [0, 2])
+    sel = sfft.select(p, 10, 0.5, "abs")          # key >= 0.25
+    np.testing.assert_array_equal(sel.chosen, [0, 1, 2, 3, 4, 5])
+    sel = sfft.select(p, 10, 0.5, "rel")          # key >= 0.25 * 9
+    np.testing.assert_array_equal(sel.chosen, [0, 2, 3, 5])
+    elig = np.array([0, 1, 1, 1, 1, 1, 1], dtype=bool)
+    sel = sfft.select(p, 2, 0.0, "abs", elig)
+    np.testing.assert_array_equal(sel.chosen, [2, 5])
+
+
+def test_candidate_product_is_lexicographic():
+    pre = np.array([[-1, 2], [0, -3], [0, 4]])
+    last = np.array([-2, 1])
+    J = sfft.candidates(pre, last)
+    assert J.shape == (6, 3)
+    order = np.lexsort(J.T[::-1])
+    np.testing.assert_array_equal(order, np.arange(6))
+    np.testing.assert_array_equal(J[3], [0, -3, 1])
+
+
+def test_noise_shared_node_zero():
+    J = np.array([[0, 1], [2, -1], [1, 1]])
+    ml = lattice.search(J, seed=1, t=2)
+    eta = sfft.lattice_noise(1, 2, 0, ml, sigma=1.0)
+    for e in eta[1:]:
+        assert e[0] == eta[0][0]
+    assert eta[0][1] != eta[1][1]
+
+
+@pytest.mark.slow
+def test_table_5_1_sample_count_and_error():
+    """Table 5.1 / Fig 5.1 (d = 5, N = 32, s = 1000, delta = 1e-12, r = 1,
+    Re/Im uniform in [-1, 1)): the paper's maximum over 10 runs is 4,525,799
+    samples (4,647,753 in Fig 5.1) with relative l2 error <= 5.3e-16.  One run
+    must use no more samples than that maximum and at least 60 % of it, and
+    recover the support exactly."""
+    sig = W.planted_signal(5, 32, 1000, seed=0, model="box")
+    res = sfft.sfft(sig, 1000, 1000, 1, 10, 1e-12, "abs", seed=0)
+    np.testing.assert_array_equal(res.freqs, sig.freqs.astype(np.int64))
+    assert 0.6 * 4_647_753 <= res.samples <= 4_647_753
+    err = np.linalg.norm(res.coeffs - sig.coeffs) / np.linalg.norm(sig.coeffs)
+    assert err < 1e-15
+
+
+@pytest.mark.slow
+def test_table_5_2_success_behaviour():
+    """Table 5.2 (d = 5, s = 1000, unimodular): r = 1, delta = 0.3 never
+    detects all frequencies (success rate 0.000, min 876 correct); r = 3,
+    delta = 1e-2 always does (success rate 1.000)."""
+    sig = W.planted_signal(5, 32, 1000, seed=100, model="unimodular")
+    truth = set(map(tuple, sig.freqs.astype(int).tolist()))
+    res = sfft.sfft(sig, 1000, 1000, 1, 10, 0.3, "abs", seed=100)
+    got = set(map(tuple, res.freqs.tolist()))
+    assert 876 <= len(got & truth) < 1000
+    res = sfft.sfft(sig, 1000, 1000, 3, 10, 1e-2, "abs", seed=100)
+    assert set(map(tuple, res.freqs.tolist())) == truth
+
+
+# ----------------------------------------------------------------------------
+# Planted mistakes: each pin above must fail when the oracle is wrong.
+# ----------------------------------------------------------------------------
+
+def _recovery_ok(dft="fft"):
+    sig, p = W.workload("tiny_d3", 1)
+    try:
+        res = _run(sig, p, 1, dft)
+    except Exception:
+        return False
+    if not np.array_equal(res.freqs, sig.freqs.astype(np.int64)):
+        return False
+    return np.max(np.abs(res.coeffs - sig.coeffs) / np.abs(sig.coeffs)) < 1e-13
+
+
+def test_mutation_dropped_average(monkeypatch):
+    orig = lattice.reconstruct
+
+    def bad(J, ml, ys, dft="fft"):
+        out, counter = orig(J, ml, ys, dft)
+        return out * np.maximum(counter, 1), counter      # forgets the 1/counter
+    monkeypatch.setattr(lattice, "reconstruct", bad)
+    assert not _recovery_ok()
+
+
+def test_mutation_wrong_dft_sign(monkeypatch):
+    monkeypatch.setattr(lattice, "lattice_dft_fft",
+                        lambda y, M, rr: (np.fft.ifft(y))[np.asarray(rr)])
+    assert not _recovery_ok()
+
+
+def test_mutation_transposed_residue(monkeypatch):
+    orig = lattice.residues
+    monkeypatch.setattr(lattice, "residues",
+                        lambda J, z, M: orig(np.asarray(J)[:, ::-1], z, M))
+    # the direct tier samples p at the true nodes, so the swapped residues no
+    # longer cancel between sampler and reconstruction
+    assert not _recovery_ok("direct")
+
+
+def test_mutation_small_lambda(monkeypatch):
+    orig = lattice.lmax_lambda
+    monkeypatch.setattr(lattice, "lmax_lambda", lambda n, c=2.0, g=0.5: (orig(n)[0], 0.5 * (n - 1)))
+    sig = W.planted_signal(5, 32, 1000, seed=0, model="box")
+    # a wrong lambda changes the sample count by about 4x: the Table 5.1 pin bites
+    res = sfft.sfft(sig, 1000, 1000, 1, 10, 1e-12, "abs", seed=0)
+    assert not (0.6 * 4_647_753 <= res.samples <= 4_647_753)
+
+
+def _line_identity_ok():
+    try:
+        test_line_coefficients_projection_identity()
+    except AssertionError:
+        return False
+    return True
+
+
+def test_mutation_missing_line_scale(monkeypatch):
+    orig = sfft.line_coefficients
+    monkeypatch.setattr(sfft, "line_coefficients", lambda y, N: orig(y, N) * (2 * N + 1))
+    # without 1/K_t the Eq. 4.2 projection identity no longer holds
+    assert not _line_identity_ok()
+
+
+def test_mutation_line_sign(monkeypatch):
+    monkeypatch.setattr(sfft, "line_coefficients",
+                        lambda y, N: np.fft.ifft(y)[np.mod(np.arange(-N, N + 1), 2 * N + 1)])
+    assert not _line_identity_ok()
