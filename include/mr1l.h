@@ -1,0 +1,244 @@
+/*
+ * mr1l.h - C ABI of the GB300 multiple rank-1 lattice sparse FFT library.
+ *
+ * Operations follow Kaemmerer, Potts, Volkmer, "High-dimensional sparse FFT
+ * based on sampling along multiple rank-1 lattices":
+ *   - a rank-1 lattice Lambda(z, M) = { j z / M mod 1 : j = 0..M-1 } and the
+ *     multiple rank-1 lattice (union of L of them), Section 2.1;
+ *   - Algorithm 1 (randomized construction, prime set of Eq. 2.2);
+ *   - Algorithm 2 (inverse multiple rank-1 lattice FFT, "reconstruct");
+ *   - lattice evaluation of a trigonometric polynomial (the aliasing
+ *     derivation of Section 4.1) and the adjoint of Algorithm 2;
+ *   - Algorithm 3 (dimension-incremental sparse FFT, "sfft_dimincr").
+ *
+ * Conventions
+ *   - Every function returns an int status (MR1L_OK = 0 on success).  No C++
+ *     exception crosses this boundary.  mr1l_last_error() copies a message
+ *     describing the last failure of the calling thread.
+ *   - Complex numbers are interleaved fp64 pairs (re, im), 16 bytes each; the
+ *     arrays must be 16-byte aligned.
+ *   - "device" pointers are CUDA global memory of the current device, owned
+ *     by the caller; "host" pointers are ordinary host memory, owned by the
+ *     caller and only read during the call.  A plan owns its own device
+ *     buffers and frees them in mr1l_destroy().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Transforms are asynchronous on that stream; plan creation
+ *     and sfft_dimincr synchronise it.
+ *   - Lattice sample vectors are stored per lattice: lattice l occupies
+ *     positions [off_l, off_l + M_l) with off_l = M_0 + .. + M_{l-1}, node j
+ *     of lattice l at off_l + j.  Node 0 (x = 0) belongs to every lattice and
+ *     is stored once per lattice.  With nrhs right-hand sides the vectors are
+ *     stacked: rhs h starts at h * sum_l M_l.
+ *   - Frequencies are rows of int32 (row-major [n][t]).
+ *
+ * Every routine fails with MR1L_E_INVAL on invalid arguments, MR1L_E_NOMEM
+ * when a device allocation fails and MR1L_E_CUDA when a CUDA call or kernel
+ * reports an error; the message names the cause.
+ */
+#ifndef MR1L_H
+#define MR1L_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MR1L_OK 0
+#define MR1L_E_INVAL 1
+#define MR1L_E_NOMEM 2
+#define MR1L_E_CUDA 3
+#define MR1L_E_NOT_RECONSTRUCTING 4
+#define MR1L_E_SAMPLER 5
+#define MR1L_E_TIMEOUT 6
+
+/* plan flags */
+#define MR1L_STRICT 1           /* fail with E_NOT_RECONSTRUCTING unless condition (2.1) holds */
+
+/* evaluation modes */
+#define MR1L_EVAL 0
+#define MR1L_ADJOINT 1
+
+/* threshold modes of sfft_dimincr */
+#define SFFT_THETA_ABS 0        /* keep |p~| >= theta (the paper's absolute delta) */
+#define SFFT_THETA_REL 1        /* keep |p~| >= theta * max |p~| of the pass */
+
+typedef struct mr1l_plan_s mr1l_plan_t;
+
+/* Copies a NUL-terminated description of the calling thread's last error into
+ * buf (at most len bytes).  Returns the status code of that error. */
+int mr1l_last_error(char* buf, size_t len);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int mr1l_version(void);
+
+/*
+ * mr1l_plan - plan the transforms on a given multiple rank-1 lattice.
+ * Section 2.1 (lattices, reconstruction property), Algorithm 2 (I_l, counter).
+ *   I     host int32 [nI][t]: the frequency set, pairwise distinct, |k_j| < 2^15.
+ *   L     number of rank-1 lattices, 1 <= L <= 64.
+ *   M     host int64 [L]: lattice sizes, pairwise distinct primes, 2 <= M_l < 2^31.
+ *   z     host int64 [L][t]: generating vectors with 0 <= z < M_l.
+ *   flags MR1L_STRICT: fail with MR1L_E_NOT_RECONSTRUCTING (and no plan) when
+ *         some k in I lies in no I_l.  Without it such k get coefficient 0.
+ * Computes the residues k.z_l mod M_l, the collision-free sets I_l and the
+ * per-frequency counters on the GPU, and the Bluestein chirp and filter tables
+ * of every lattice.  *out receives the plan; destroy it with mr1l_destroy.
+ */
+int mr1l_plan(const int32_t* I, int64_t nI, int t, int L, const int64_t* M, const int64_t* z,
+              int flags, void* stream, mr1l_plan_t** out);
+
+/*
+ * mr1l_plan_search - build the lattice by Algorithm 1 (c, gamma), repeated up
+ * to b times until condition (2.1) holds (step 2b of Algorithm 3).  The prime
+ * sizes are the Lmax smallest primes above lambda = c (|I| - 1) on which
+ * k -> k mod p is injective (Eq. 2.2); z_l is drawn uniformly from
+ * [1, M_l - 1]^t as 1 + (u mod (M_l - 1)), u the first 64-bit word of
+ * Philox4x32-10 with key = seed and counter (j, l, attempt, 3 << 24 | t).
+ * When all b searches fail the last one is kept (flags MR1L_STRICT turns that
+ * into MR1L_E_NOT_RECONSTRUCTING).
+ */
+int mr1l_plan_search(const int32_t* I, int64_t nI, int t, double c, double gamma, int b,
+                     uint64_t seed, int flags, void* stream, mr1l_plan_t** out);
+
+/*
+ * mr1l_plan_info - L, the lattice sizes (M_out: host int64 [64], may be NULL),
+ * generating vectors (z_out: host int64 [L][t], may be NULL), the node count
+ * 1 - L + sum M_l, the total sample-vector length sum M_l and the number of
+ * frequencies that no lattice covers.  Any output pointer may be NULL.
+ */
+int mr1l_plan_info(const mr1l_plan_t* plan, int* L, int64_t* M_out, int64_t* z_out,
+                   int64_t* nodes, int64_t* sum_M, int64_t* n_uncovered);
+
+/* mr1l_plan_masks - the collision-free sets as bitmasks (host uint64 [nI]:
+ * bit l set iff k in I_l) and, optionally, the residues (host uint32 [L][nI]). */
+int mr1l_plan_masks(const mr1l_plan_t* plan, uint64_t* masks, uint32_t* residues);
+
+void mr1l_destroy(mr1l_plan_t* plan);
+
+/*
+ * mr1l_reconstruct - Algorithm 2 on the GPU.
+ *   y  device complex [nrhs][sum_l M_l]: samples p(j z_l / M_l mod 1).
+ *   c  device complex [nrhs][nI]: p~_k = (1/counter_k) sum_{l: k in I_l}
+ *      (1/M_l) sum_j y_{l,j} exp(-2 pi i j k.z_l / M_l);  0 where counter_k = 0.
+ * Each length-M_l DFT runs as a Bluestein convolution over power-of-two FP64
+ * FFTs; the gather of the averaged coefficients is fused with the final chirp.
+ */
+int mr1l_reconstruct(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* stream);
+
+/*
+ * mr1l_evaluate - lattice evaluation and the adjoint of Algorithm 2.
+ *   c  device complex [nrhs][nI], y device complex [nrhs][sum_l M_l].
+ *   MR1L_EVAL:    y_{l,j} = sum_{k in I} c_k exp(2 pi i j k.z_l / M_l)
+ *                 (the polynomial sum_k c_k e^{2 pi i k.x} at the nodes);
+ *   MR1L_ADJOINT: y_{l,j} = sum_{k in I_l} c_k / (counter_k M_l) exp(2 pi i j k.z_l / M_l)
+ *                 (the conjugate transpose of mr1l_reconstruct).
+ */
+int mr1l_evaluate(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3                                                               */
+/* ------------------------------------------------------------------------ */
+
+#define SFFT_REQ_LINE 0
+#define SFFT_REQ_LATTICE 1
+
+/* A request for samples of the black-box function p (Algorithm 3, steps 1,
+ * 2a and 2c-2d).  Anchors are the random components x' (all d entries are
+ * given; the entries the nodes replace are ignored).
+ *   LINE:    nodes (x'_1, .., x'_{t-1}, l / K, x'_{t+1}, .., x'_d), l = 0..K-1;
+ *            y receives K values.
+ *   LATTICE: nodes (j z_l / M_l mod 1, x'_{t+1}, .., x'_d) for every lattice l
+ *            and j = 0..M_l - 1, stored per lattice as above (sum M_l values).
+ * y is a device pointer into library memory, valid during the callback; the
+ * callback must enqueue its work on `stream` (or finish it before returning). */
+typedef struct sfft_request {
+    int kind;               /* SFFT_REQ_LINE or SFFT_REQ_LATTICE */
+    int t;                  /* 1-based dimension increment */
+    int rep;                /* 0-based detection iteration */
+    int d;
+    const double* anchors;  /* host double [d] */
+    int K;                  /* LINE: number of nodes */
+    int L;                  /* LATTICE: lattices, sizes and generating vectors */
+    const int64_t* M;       /* host int64 [L] */
+    const int64_t* z;       /* host int64 [L][t] */
+    int64_t sum_M;
+} sfft_request;
+
+typedef int (*sfft_sample_fn)(void* user, const sfft_request* req, void* y, void* stream);
+
+/* Sampler: either a user callback, or (fn == NULL) the built-in planted
+ * sparse polynomial p(x) = sum_h c_h e^{2 pi i h.x} plus complex Gaussian
+ * noise eta = sigma/sqrt(2) (g1 + i g2) (Section 5.2), drawn with Philox
+ * purposes 4 and 5 keyed by noise_seed.  The planted sampler evaluates
+ * lattices by the Section 4.1 aliasing identity (bin h_(1..t).z_l mod M_l,
+ * weight c_h e^{2 pi i h_(>t).x'}) and an inverse Bluestein DFT. */
+typedef struct sfft_sampler {
+    sfft_sample_fn fn;
+    void* user;
+    const int32_t* freqs;   /* planted: host int32 [s][d] */
+    const double* coeffs;   /* planted: host complex [s] */
+    int64_t s;
+    double sigma;
+    uint64_t noise_seed;
+} sfft_sampler;
+
+typedef struct sfft_params {
+    int d;                  /* dimension, >= 2 */
+    int N;                  /* search domain Gamma = {-N..N}^d, 1 <= N <= 2048 */
+    int64_t s;              /* sparsity parameter (final cap) */
+    int64_t s_local;        /* per-pass cap for t < d (paper default: s) */
+    int r;                  /* detection iterations */
+    int b;                  /* lattice searches per increment (total) */
+    double theta;           /* threshold */
+    int theta_mode;         /* SFFT_THETA_ABS or SFFT_THETA_REL */
+    uint64_t seed;          /* Philox key of anchors and generating vectors */
+    int batch_reps;         /* 0: one repetition per launch sequence; 1: all r~ fused */
+} sfft_params;
+
+#define SFFT_MAX_STEPS 256
+
+typedef struct sfft_step_stats {
+    int t;
+    int n_line;             /* |I^(t)| */
+    int64_t n_cand;         /* |J_t| */
+    int L;
+    int attempts;
+    int covered;
+    int64_t sum_M;
+    int64_t samples;        /* samples requested at this increment */
+    int64_t n_detected;     /* |I^(1..t)| */
+} sfft_step_stats;
+
+typedef struct sfft_stats {
+    int n_steps;
+    int64_t samples;        /* total samples, distinct nodes counted once */
+    double ms_total;
+    double ms_sampling;     /* time inside the sampler (GPU events) */
+    sfft_step_stats steps[SFFT_MAX_STEPS];
+} sfft_stats;
+
+typedef struct sfft_result {
+    int64_t n;              /* detected frequencies */
+    int d;
+    int32_t* freqs;         /* host int32 [n][d], lexicographic */
+    double* coeffs;         /* host complex [n] */
+    sfft_stats stats;
+} sfft_result;
+
+/*
+ * sfft_dimincr - Algorithm 3 on the GPU.  The detected set and its
+ * coefficients (those of the single pass at t = d) are returned in a result
+ * owned by the library; release it with sfft_free.
+ */
+int sfft_dimincr(const sfft_params* params, const sfft_sampler* sampler, void* stream,
+                 sfft_result** out);
+
+void sfft_free(sfft_result* res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MR1L_H */

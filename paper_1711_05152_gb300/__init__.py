@@ -1,0 +1,307 @@
+"""Python binding of the mr1l CUDA library (multiple rank-1 lattice sparse FFT).
+
+Argument marshalling only: every step of the transforms runs in the CUDA
+kernels of ``libmr1l.so`` (built in-tree by ``build.py``).  PyTorch provides
+device memory and streams.  There is no CPU fallback: importing the binding
+raises when the library has not been built.
+
+Names follow the paper (Kaemmerer, Potts, Volkmer): ``plan`` builds a
+multiple rank-1 lattice for a frequency set I (given lattices, or Algorithm 1
+with ``plan_search``), ``Plan.reconstruct`` is Algorithm 2, ``Plan.evaluate``
+the lattice evaluation and its adjoint, and ``sfft_dimincr`` Algorithm 3.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmr1l.so")
+
+MR1L_OK = 0
+MR1L_E_INVAL = 1
+MR1L_E_NOMEM = 2
+MR1L_E_CUDA = 3
+MR1L_E_NOT_RECONSTRUCTING = 4
+MR1L_E_SAMPLER = 5
+MR1L_E_TIMEOUT = 6
+MR1L_STRICT = 1
+MR1L_EVAL = 0
+MR1L_ADJOINT = 1
+SFFT_THETA_ABS = 0
+SFFT_THETA_REL = 1
+SFFT_REQ_LINE = 0
+SFFT_REQ_LATTICE = 1
+SFFT_MAX_STEPS = 256
+
+EXPORTS = [
+    "mr1l_last_error", "mr1l_version", "mr1l_plan", "mr1l_plan_search", "mr1l_plan_info",
+    "mr1l_plan_masks", "mr1l_destroy", "mr1l_reconstruct", "mr1l_evaluate", "sfft_dimincr",
+    "sfft_free",
+]
+
+
+class Mr1lError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mr1l error {code}: {msg}")
+        self.code = code
+
+
+class sfft_request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("t", C.c_int), ("rep", C.c_int), ("d", C.c_int),
+                ("anchors", C.POINTER(C.c_double)), ("K", C.c_int), ("L", C.c_int),
+                ("M", C.POINTER(C.c_int64)), ("z", C.POINTER(C.c_int64)), ("sum_M", C.c_int64)]
+
+
+SAMPLE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(sfft_request), C.c_void_p, C.c_void_p)
+
+
+class sfft_sampler(C.Structure):
+    _fields_ = [("fn", SAMPLE_FN), ("user", C.c_void_p), ("freqs", C.POINTER(C.c_int32)),
+                ("coeffs", C.POINTER(C.c_double)), ("s", C.c_int64), ("sigma", C.c_double),
+                ("noise_seed", C.c_uint64)]
+
+
+class sfft_params(C.Structure):
+    _fields_ = [("d", C.c_int), ("N", C.c_int), ("s", C.c_int64), ("s_local", C.c_int64),
+                ("r", C.c_int), ("b", C.c_int), ("theta", C.c_double), ("theta_mode", C.c_int),
+                ("seed", C.c_uint64), ("batch_reps", C.c_int)]
+
+
+class sfft_step_stats(C.Structure):
+    _fields_ = [("t", C.c_int), ("n_line", C.c_int), ("n_cand", C.c_int64), ("L", C.c_int),
+                ("attempts", C.c_int), ("covered", C.c_int), ("sum_M", C.c_int64),
+                ("samples", C.c_int64), ("n_detected", C.c_int64)]
+
+
+class sfft_stats(C.Structure):
+    _fields_ = [("n_steps", C.c_int), ("samples", C.c_int64), ("ms_total", C.c_double),
+                ("ms_sampling", C.c_double), ("steps", sfft_step_stats * SFFT_MAX_STEPS)]
+
+
+class sfft_result(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int), ("freqs", C.POINTER(C.c_int32)),
+                ("coeffs", C.POINTER(C.c_double)), ("stats", sfft_stats)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmr1l.so not built ({LIB_PATH}); run paper_1711_05152_gb300/build.py")
+    L = C.CDLL(LIB_PATH)
+    vp, i32p, i64p = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    L.mr1l_last_error.argtypes = [C.c_char_p, C.c_size_t]
+    L.mr1l_version.argtypes = []
+    L.mr1l_plan.argtypes = [i32p, C.c_int64, C.c_int, C.c_int, i64p, i64p, C.c_int, vp, C.POINTER(vp)]
+    L.mr1l_plan_search.argtypes = [i32p, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int, C.c_uint64,
+                                   C.c_int, vp, C.POINTER(vp)]
+    L.mr1l_plan_info.argtypes = [vp, C.POINTER(C.c_int), i64p, i64p, i64p, i64p, i64p]
+    L.mr1l_plan_masks.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]
+    L.mr1l_destroy.argtypes = [vp]
+    L.mr1l_destroy.restype = None
+    L.mr1l_reconstruct.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.mr1l_evaluate.argtypes = [vp, vp, C.c_int, vp, C.c_int, vp]
+    L.sfft_dimincr.argtypes = [C.POINTER(sfft_params), C.POINTER(sfft_sampler), vp,
+                               C.POINTER(C.POINTER(sfft_result))]
+    L.sfft_free.argtypes = [C.POINTER(sfft_result)]
+    L.sfft_free.restype = None
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != MR1L_OK:
+        buf = C.create_string_buffer(1024)
+        lib().mr1l_last_error(buf, 1024)
+        raise Mr1lError(rc, buf.value.decode(errors="replace"))
+
+
+def _stream(stream=None) -> int:
+    """cudaStream_t of a torch stream (default: the current one); a plain int
+    is taken as the raw handle (0 = legacy default stream)."""
+    if isinstance(stream, int):
+        return stream
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+def _i64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int64)
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class Plan:
+    """A multiple rank-1 lattice planned for a frequency set I (rows of Z^t)."""
+
+    def __init__(self, handle: int, nI: int, t: int):
+        self._h = C.c_void_p(handle)
+        self.nI = nI
+        self.t = t
+        info = self.info()
+        self.L = info["L"]
+        self.M = info["M"]
+        self.z = info["z"]
+        self.sum_M = info["sum_M"]
+        self.nodes = info["nodes"]
+        self.n_uncovered = info["n_uncovered"]
+
+    def info(self) -> dict:
+        L = C.c_int()
+        M = np.zeros(64, dtype=np.int64)
+        nodes, sum_M, unc = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().mr1l_plan_info(self._h, C.byref(L), _ptr(M, C.c_int64), None, C.byref(nodes),
+                                    C.byref(sum_M), C.byref(unc)))
+        z = np.zeros(L.value * self.t, dtype=np.int64)
+        _check(lib().mr1l_plan_info(self._h, None, None, _ptr(z, C.c_int64), None, None, None))
+        return dict(L=L.value, M=M[:L.value].copy(), z=z.reshape(L.value, self.t), nodes=nodes.value,
+                    sum_M=sum_M.value, n_uncovered=unc.value)
+
+    def masks(self):
+        """(bitmask of lattices where each k is collision-free, residues [L][nI])."""
+        m = np.zeros(self.nI, dtype=np.uint64)
+        r = np.zeros((self.L, self.nI), dtype=np.uint32)
+        _check(lib().mr1l_plan_masks(self._h, _ptr(m, C.c_uint64), _ptr(r, C.c_uint32)))
+        return m, r
+
+    def reconstruct(self, y, out=None, stream=None):
+        """Algorithm 2: y complex128 [nrhs, sum_M] (or [sum_M]) on the GPU -> c [nrhs, nI]."""
+        import torch
+        squeeze = y.dim() == 1
+        y2 = y.reshape(-1, self.sum_M)
+        if y2.dtype != torch.complex128 or not y2.is_cuda or not y2.is_contiguous():
+            raise TypeError("y must be a contiguous complex128 CUDA tensor")
+        nrhs = y2.shape[0]
+        if out is None:
+            out = torch.empty((nrhs, self.nI), dtype=torch.complex128, device=y.device)
+        _check(lib().mr1l_reconstruct(self._h, C.c_void_p(y2.data_ptr()), nrhs, C.c_void_p(out.data_ptr()),
+                                      C.c_void_p(_stream(stream))))
+        return out[0] if squeeze else out
+
+    def evaluate(self, c, mode: int = MR1L_EVAL, out=None, stream=None):
+        """Lattice evaluation (mode MR1L_EVAL) or the adjoint of Algorithm 2
+        (MR1L_ADJOINT): c complex128 [nrhs, nI] -> y [nrhs, sum_M]."""
+        import torch
+        squeeze = c.dim() == 1
+        c2 = c.reshape(-1, self.nI)
+        if c2.dtype != torch.complex128 or not c2.is_cuda or not c2.is_contiguous():
+            raise TypeError("c must be a contiguous complex128 CUDA tensor")
+        nrhs = c2.shape[0]
+        if out is None:
+            out = torch.empty((nrhs, self.sum_M), dtype=torch.complex128, device=c.device)
+        _check(lib().mr1l_evaluate(self._h, C.c_void_p(c2.data_ptr()), nrhs, C.c_void_p(out.data_ptr()),
+                                   mode, C.c_void_p(_stream(stream))))
+        return out[0] if squeeze else out
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().mr1l_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan(I, M, z, strict: bool = False, stream=None) -> Plan:
+    """Plan on given lattices (sizes M [L], generating vectors z [L, t])."""
+    I = _i32(I)
+    if I.ndim == 1:
+        I = I.reshape(-1, 1)
+    n, t = I.shape
+    M = _i64(M).reshape(-1)
+    z = _i64(z).reshape(M.shape[0], t)
+    h = C.c_void_p()
+    _check(lib().mr1l_plan(_ptr(I, C.c_int32), n, t, M.shape[0], _ptr(M, C.c_int64), _ptr(z, C.c_int64),
+                           MR1L_STRICT if strict else 0, C.c_void_p(_stream(stream)), C.byref(h)))
+    return Plan(h.value, n, t)
+
+
+def plan_search(I, seed: int, c: float = 2.0, gamma: float = 0.5, b: int = 10, strict: bool = False,
+                stream=None) -> Plan:
+    """Plan on a lattice built by Algorithm 1 (up to b searches)."""
+    I = _i32(I)
+    if I.ndim == 1:
+        I = I.reshape(-1, 1)
+    n, t = I.shape
+    h = C.c_void_p()
+    _check(lib().mr1l_plan_search(_ptr(I, C.c_int32), n, t, c, gamma, b, seed, MR1L_STRICT if strict else 0,
+                                  C.c_void_p(_stream(stream)), C.byref(h)))
+    return Plan(h.value, n, t)
+
+
+@dataclasses.dataclass
+class SfftOutput:
+    freqs: np.ndarray          # int64 [n, d]
+    coeffs: np.ndarray         # complex128 [n]
+    samples: int
+    ms_total: float
+    ms_sampling: float
+    steps: list
+
+
+def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str = "rel", seed: int = 0,
+                 s_local: int | None = None, b: int = 10, freqs=None, coeffs=None, sigma: float = 0.0,
+                 noise_seed: int | None = None, sampler=None, batch_reps: bool = False,
+                 stream=None) -> SfftOutput:
+    """Algorithm 3.  Either a planted polynomial (freqs [s, d], coeffs [s],
+    sigma) evaluated by the library, or ``sampler(req, y_ptr, stream_ptr)``,
+    a Python callable that fills the device buffer y_ptr for a request."""
+    p = sfft_params(d=d, N=N, s=s, s_local=s if s_local is None else s_local, r=r, b=b, theta=theta,
+                    theta_mode=SFFT_THETA_REL if theta_mode == "rel" else SFFT_THETA_ABS, seed=seed,
+                    batch_reps=1 if batch_reps else 0)
+    keep = []
+    if sampler is None:
+        f = _i32(freqs).reshape(-1, d)
+        c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.complex128)).view(np.float64)
+        keep += [f, c]
+        samp = sfft_sampler(SAMPLE_FN(), None, _ptr(f, C.c_int32), _ptr(c, C.c_double), f.shape[0], sigma,
+                            seed if noise_seed is None else noise_seed)
+    else:
+        def _cb(user, req, y, stream_ptr):
+            try:
+                return int(sampler(req.contents, y, stream_ptr) or 0)
+            except Exception:  # reported as a sampler failure
+                import traceback
+                traceback.print_exc()
+                return 1
+        fn = SAMPLE_FN(_cb)
+        keep.append(fn)
+        samp = sfft_sampler(fn, None, None, None, 0, 0.0, 0)
+    out = C.POINTER(sfft_result)()
+    _check(lib().sfft_dimincr(C.byref(p), C.byref(samp), C.c_void_p(_stream(stream)), C.byref(out)))
+    try:
+        res = out.contents
+        n = res.n
+        fr = np.ctypeslib.as_array(res.freqs, shape=(max(n, 1) * d,))[: n * d].astype(np.int64).reshape(n, d)
+        cf = np.ctypeslib.as_array(res.coeffs, shape=(max(n, 1) * 2,))[: 2 * n].copy().view(np.complex128)
+        st = res.stats
+        steps = []
+        for i in range(st.n_steps):
+            x = st.steps[i]
+            steps.append(dict(t=x.t, n_line=x.n_line, n_cand=x.n_cand, L=x.L, attempts=x.attempts,
+                              covered=bool(x.covered), sum_M=x.sum_M, samples=x.samples,
+                              n_detected=x.n_detected))
+        return SfftOutput(fr, cf, st.samples, st.ms_total, st.ms_sampling, steps)
+    finally:
+        lib().sfft_free(out)

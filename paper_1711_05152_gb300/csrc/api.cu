@@ -1,0 +1,785 @@
+// C ABI of the library: plans on multiple rank-1 lattices (Algorithms 1, 2,
+// lattice evaluation and adjoint) and the dimension-incremental sparse FFT
+// driver (Algorithm 3).  Host code here only orchestrates: every step of the
+// transforms runs in the CUDA kernels of fft.cu, lattice.cu and select.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "ops.cuh"
+
+namespace mr1l {
+
+// ---------------------------------------------------------------------------
+// Last error (per thread)
+// ---------------------------------------------------------------------------
+static thread_local int tl_code = MR1L_OK;
+static thread_local std::string tl_msg;
+
+void set_last_error(int code, const std::string& msg) {
+  tl_code = code;
+  tl_msg = msg;
+}
+
+template <typename F>
+static int guarded(F&& f) {
+  try {
+    f();
+    return MR1L_OK;
+  } catch (const Error& e) {
+    set_last_error(e.code, e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error(MR1L_E_NOMEM, "host allocation failed");
+    return MR1L_E_NOMEM;
+  } catch (const std::exception& e) {
+    set_last_error(MR1L_E_CUDA, e.what());
+    return MR1L_E_CUDA;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 host logic: Lmax, lambda, the prime set of Eq. 2.2, z draws.
+// ---------------------------------------------------------------------------
+static bool is_prime_u64(int64_t p) {
+  if (p < 2) return false;
+  if (p % 2 == 0) return p == 2;
+  if (p % 3 == 0) return p == 3;
+  for (int64_t f = 5; f * f <= p; f += 6)
+    if (p % f == 0 || p % (f + 2) == 0) return false;
+  return true;
+}
+
+static void lmax_lambda(int64_t n, double c, double gamma, int& Lmax, double& lam) {
+  Lmax = (int)std::ceil(c * c / ((c - 1.0) * (c - 1.0)) * (std::log((double)n) - std::log(gamma)) / 2.0);
+  lam = c * (double)(n - 1);
+}
+
+// Rows of the candidate set on the host (only needed for the injectivity
+// test of small primes; rows are produced on demand from prefix x last).
+struct HostRows {
+  const int32_t* pre;
+  int tp;
+  int64_t np;
+  const int32_t* last;  // may be null
+  int64_t nq;
+  int t() const { return tp + (last ? 1 : 0); }
+  int64_t n() const { return np * nq; }
+  void row(int64_t c, int32_t* out) const {
+    int64_t p = c / nq, q = c - p * nq;
+    for (int j = 0; j < tp; ++j) out[j] = pre[p * tp + j];
+    if (last) out[tp] = last[q];
+  }
+};
+
+// k -> k mod p componentwise injective on J (membership in P^J)
+static bool injective_mod(const HostRows& J, int64_t p) {
+  const int64_t n = J.n();
+  if (n <= 1) return true;
+  const int t = J.t();
+  // expansion: a prime above every component range is injective
+  int64_t expansion = 0;
+  std::vector<int32_t> row(t);
+  std::vector<int64_t> lo(t, INT64_MAX), hi(t, INT64_MIN);
+  for (int64_t c = 0; c < n; ++c) {
+    J.row(c, row.data());
+    for (int j = 0; j < t; ++j) {
+      lo[j] = std::min<int64_t>(lo[j], row[j]);
+      hi[j] = std::max<int64_t>(hi[j], row[j]);
+    }
+  }
+  for (int j = 0; j < t; ++j) expansion = std::max(expansion, hi[j] - lo[j]);
+  if (p > expansion) return true;
+  std::vector<std::vector<int64_t>> red(n, std::vector<int64_t>(t));
+  for (int64_t c = 0; c < n; ++c) {
+    J.row(c, row.data());
+    for (int j = 0; j < t; ++j) red[c][j] = ((row[j] % p) + p) % p;
+  }
+  std::sort(red.begin(), red.end());
+  return std::adjacent_find(red.begin(), red.end()) == red.end();
+}
+
+static std::vector<int> prime_set(const HostRows& J, double lam, int Lmax) {
+  std::vector<int> out;
+  int64_t p = (int64_t)std::floor(lam) + 1;
+  bool checked_expansion = false;
+  int64_t expansion_ok_from = INT64_MAX;
+  while ((int)out.size() < Lmax) {
+    if (is_prime_u64(p)) {
+      bool ok;
+      if (checked_expansion && p >= expansion_ok_from) {
+        ok = true;
+      } else {
+        ok = injective_mod(J, p);
+        // once a prime beyond the expansion is reached all larger ones pass
+        if (!checked_expansion) {
+          checked_expansion = true;
+          int64_t expansion = 0;
+          const int t = J.t();
+          std::vector<int32_t> row(t);
+          std::vector<int64_t> lo(t, INT64_MAX), hi(t, INT64_MIN);
+          for (int64_t c = 0; c < J.n(); ++c) {
+            J.row(c, row.data());
+            for (int j = 0; j < t; ++j) {
+              lo[j] = std::min<int64_t>(lo[j], row[j]);
+              hi[j] = std::max<int64_t>(hi[j], row[j]);
+            }
+          }
+          for (int j = 0; j < t; ++j) expansion = std::max(expansion, hi[j] - lo[j]);
+          expansion_ok_from = expansion + 1;
+        }
+      }
+      if (ok) {
+        MR1L_REQUIRE(p < (int64_t(1) << 31), "lattice size exceeds 2^31");
+        out.push_back((int)p);
+      }
+    }
+    ++p;
+  }
+  return out;
+}
+
+static void draw_z(uint64_t seed, int t, int attempt, const std::vector<int>& M, std::vector<int64_t>& z) {
+  z.assign(M.size() * t, 0);
+  for (size_t l = 0; l < M.size(); ++l)
+    for (int j = 0; j < t; ++j) {
+      U64Pair u = philox_u64(seed, kZvec, (uint32_t)t, (uint32_t)j, (uint32_t)l, (uint32_t)attempt);
+      z[l * t + j] = 1 + (int64_t)(u.a % (uint64_t)(M[l] - 1));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Lattice workspace: residues, collisions, coverage, Bluestein tables.
+// ---------------------------------------------------------------------------
+struct LatticeWork {
+  int t = 0, L = 0, Luse = 0;
+  std::vector<int> Mh;
+  std::vector<int64_t> zh, offh;
+  int64_t words = 0, sumM_all = 0, sumM = 0;
+  int Lneed = 0, n_uncovered = 0;
+  DevBuf<int> M;
+  DevBuf<int64_t> z, off, bm_off;
+  DevBuf<uint32_t> pre_res, last_res, seen;
+  DevBuf<uint64_t> umask;
+  DevBuf<int> cover;
+  DevBuf<cplx> w, ws, Bh;
+  BlueGeom geom{};
+  LatticeDev dev() {
+    LatticeDev d;
+    d.L = L;
+    d.t = t;
+    d.M = M.get();
+    d.z = z.get();
+    d.pre_res = pre_res.get();
+    d.last_res = last_res.get();
+    return d;
+  }
+
+  // Residues, collision counts and coverage of lattices (M, z) on J.
+  void load(const CandSet& J, const std::vector<int>& Ms, const std::vector<int64_t>& zs, int t_, cudaStream_t s) {
+    t = t_;
+    L = (int)Ms.size();
+    MR1L_REQUIRE(L >= 1 && L <= 64, "number of lattices must be in [1, 64]");
+    Mh = Ms;
+    zh = zs;
+    offh.assign(L, 0);
+    std::vector<int64_t> bm(L, 0);
+    sumM_all = 0;
+    words = 0;
+    for (int l = 0; l < L; ++l) {
+      offh[l] = sumM_all;
+      bm[l] = words;
+      sumM_all += Mh[l];
+      words += (Mh[l] + 31) / 32;
+    }
+    M.reserve(L);
+    z.reserve((size_t)L * t);
+    off.reserve(L);
+    bm_off.reserve(L);
+    MR1L_CUDA(cudaMemcpyAsync(M.get(), Mh.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
+    MR1L_CUDA(cudaMemcpyAsync(z.get(), zh.data(), (size_t)L * t * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MR1L_CUDA(cudaMemcpyAsync(off.get(), offh.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MR1L_CUDA(cudaMemcpyAsync(bm_off.get(), bm.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    pre_res.reserve((size_t)L * std::max<int64_t>(J.np, 1));
+    last_res.reserve((size_t)L * std::max<int64_t>(J.nq, 1));
+    seen.reserve(2 * words);
+    umask.reserve(std::max<int64_t>(J.n(), 1));
+    cover.reserve(2);
+    MR1L_CUDA(cudaMemsetAsync(seen.get(), 0, 2 * words * sizeof(uint32_t), s));
+    residues(J, dev(), s);
+    collide_and_cover(J, dev(), seen.get(), bm_off.get(), words, umask.get(), cover.get(), s);
+    int hc[2];
+    MR1L_CUDA(cudaMemcpyAsync(hc, cover.get(), sizeof(hc), cudaMemcpyDeviceToHost, s));
+    MR1L_CUDA(cudaStreamSynchronize(s));
+    Lneed = hc[0];
+    n_uncovered = hc[1];
+  }
+
+  // Chirp and filter tables of lattices 0..Luse-1.
+  void tables(int Luse_, cudaStream_t s) {
+    Luse = Luse_;
+    int maxM = 0;
+    sumM = 0;
+    for (int l = 0; l < Luse; ++l) {
+      maxM = std::max(maxM, Mh[l]);
+      sumM += Mh[l];
+    }
+    int logP = ilog2_pow2(2 * (int64_t)maxM - 1);
+    if (logP < 1) logP = 1;
+    MR1L_REQUIRE(logP <= 24, "lattice size too large for the Bluestein FFT (2 M - 1 > 2^24)");
+    geom = BlueGeom{};
+    blue_split(geom, logP);
+    geom.L = Luse;
+    geom.off = off.get();
+    geom.M = M.get();
+    w.reserve(std::max<int64_t>(sumM, 1));
+    ws.reserve(std::max<int64_t>(sumM, 1));
+    Bh.reserve((size_t)Luse * geom.P);
+    geom.w = w.get();
+    geom.ws = ws.get();
+    geom.Bh = Bh.get();
+    geom.tw = twiddle_table(logP, s);
+    geom.twn = small_twiddles(s);
+    chirp_tables(geom, maxM, s);
+    blue_filter(geom, s);
+  }
+};
+
+// Validation shared by the plan constructors.
+static void validate_set(const int32_t* I, int64_t nI, int t) {
+  MR1L_REQUIRE(I != nullptr || nI == 0, "I is null");
+  MR1L_REQUIRE(nI >= 1, "the frequency set must not be empty");
+  MR1L_REQUIRE(t >= 1 && t <= 64, "t must be in [1, 64]");
+  for (int64_t i = 0; i < nI * t; ++i) MR1L_REQUIRE(I[i] > -32768 && I[i] < 32768, "|k_j| must be < 2^15");
+  std::vector<int64_t> idx(nI);
+  for (int64_t i = 0; i < nI; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+    return std::lexicographical_compare(I + a * t, I + a * t + t, I + b * t, I + b * t + t);
+  });
+  for (int64_t i = 1; i < nI; ++i)
+    MR1L_REQUIRE(!std::equal(I + idx[i - 1] * t, I + idx[i - 1] * t + t, I + idx[i] * t),
+                 "frequencies must be pairwise distinct");
+}
+
+}  // namespace mr1l
+
+using namespace mr1l;
+
+// ---------------------------------------------------------------------------
+// Plans
+// ---------------------------------------------------------------------------
+struct mr1l_plan_s {
+  int64_t nI = 0;
+  int t = 0;
+  int flags = 0;
+  int attempts = 0;
+  DevBuf<int32_t> I;
+  LatticeWork lw;
+  // grow-only transform scratch
+  DevBuf<cplx> C, bins, work;
+  CandSet cand() const {
+    CandSet J;
+    J.tp = t;
+    J.t = t;
+    J.np = nI;
+    J.nq = 1;
+    J.pre = I.get();
+    J.last = nullptr;
+    return J;
+  }
+};
+
+static void plan_finish(mr1l_plan_t* p, int Luse, cudaStream_t s) {
+  p->lw.tables(Luse, s);
+  MR1L_CUDA(cudaStreamSynchronize(s));
+}
+
+extern "C" int mr1l_last_error(char* buf, size_t len) {
+  if (buf && len) {
+    size_t k = std::min(len - 1, tl_msg.size());
+    std::memcpy(buf, tl_msg.data(), k);
+    buf[k] = 0;
+  }
+  return tl_code;
+}
+
+extern "C" int mr1l_version(void) { return 100; }
+
+extern "C" int mr1l_plan(const int32_t* I, int64_t nI, int t, int L, const int64_t* M, const int64_t* z, int flags,
+                         void* stream, mr1l_plan_t** out) {
+  return guarded([&] {
+    MR1L_REQUIRE(out != nullptr, "out is null");
+    *out = nullptr;
+    validate_set(I, nI, t);
+    MR1L_REQUIRE(L >= 1 && L <= 64, "L must be in [1, 64]");
+    MR1L_REQUIRE(M != nullptr && z != nullptr, "M or z is null");
+    std::vector<int> Ms(L);
+    for (int l = 0; l < L; ++l) {
+      MR1L_REQUIRE(M[l] >= 2 && M[l] < (int64_t(1) << 31), "M_l must be in [2, 2^31)");
+      MR1L_REQUIRE(is_prime_u64(M[l]), "M_l must be prime");
+      for (int k = 0; k < l; ++k) MR1L_REQUIRE(M[k] != M[l], "lattice sizes must be distinct");
+      Ms[l] = (int)M[l];
+    }
+    std::vector<int64_t> zs((size_t)L * t);
+    for (int l = 0; l < L; ++l)
+      for (int j = 0; j < t; ++j) {
+        MR1L_REQUIRE(z[l * t + j] >= 0 && z[l * t + j] < M[l], "z_l must lie in [0, M_l)");
+        zs[l * t + j] = z[l * t + j];
+      }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::unique_ptr<mr1l_plan_t> p(new mr1l_plan_t());
+    p->nI = nI;
+    p->t = t;
+    p->flags = flags;
+    p->attempts = 1;
+    p->I.reserve(nI * t);
+    MR1L_CUDA(cudaMemcpyAsync(p->I.get(), I, nI * t * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    p->lw.load(p->cand(), Ms, zs, t, s);
+    if ((flags & MR1L_STRICT) && p->lw.n_uncovered)
+      throw Error(MR1L_E_NOT_RECONSTRUCTING, "the lattices do not satisfy condition (2.1) for I");
+    plan_finish(p.get(), L, s);
+    *out = p.release();
+  });
+}
+
+extern "C" int mr1l_plan_search(const int32_t* I, int64_t nI, int t, double c, double gamma, int b, uint64_t seed,
+                                int flags, void* stream, mr1l_plan_t** out) {
+  return guarded([&] {
+    MR1L_REQUIRE(out != nullptr, "out is null");
+    *out = nullptr;
+    validate_set(I, nI, t);
+    MR1L_REQUIRE(c > 1.0 && gamma > 0.0 && gamma < 1.0, "need c > 1 and 0 < gamma < 1");
+    MR1L_REQUIRE(b >= 1, "b must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::unique_ptr<mr1l_plan_t> p(new mr1l_plan_t());
+    p->nI = nI;
+    p->t = t;
+    p->flags = flags;
+    p->I.reserve(nI * t);
+    MR1L_CUDA(cudaMemcpyAsync(p->I.get(), I, nI * t * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    int Lmax;
+    double lam;
+    lmax_lambda(nI, c, gamma, Lmax, lam);
+    MR1L_REQUIRE(Lmax >= 1 && Lmax <= 64, "Lmax out of range");
+    HostRows rows{I, t, nI, nullptr, 1};
+    std::vector<int> primes = prime_set(rows, lam, Lmax);
+    std::vector<int64_t> zs;
+    for (int a = 0; a < b; ++a) {
+      draw_z(seed, t, a, primes, zs);
+      p->lw.load(p->cand(), primes, zs, t, s);
+      p->attempts = a + 1;
+      if (p->lw.n_uncovered == 0) break;
+    }
+    int Luse = p->lw.n_uncovered == 0 ? p->lw.Lneed : Lmax;
+    if (p->lw.n_uncovered && (flags & MR1L_STRICT))
+      throw Error(MR1L_E_NOT_RECONSTRUCTING, "no reconstructing lattice after b searches");
+    if (Luse < Lmax) {
+      // drop the lattices beyond the first full coverage (Algorithm 1 stops there)
+      std::vector<int> Ms(primes.begin(), primes.begin() + Luse);
+      std::vector<int64_t> z2(zs.begin(), zs.begin() + (size_t)Luse * t);
+      p->lw.load(p->cand(), Ms, z2, t, s);
+    }
+    plan_finish(p.get(), p->lw.L, s);
+    *out = p.release();
+  });
+}
+
+extern "C" int mr1l_plan_info(const mr1l_plan_t* plan, int* L, int64_t* M_out, int64_t* z_out, int64_t* nodes,
+                              int64_t* sum_M, int64_t* n_uncovered) {
+  return guarded([&] {
+    MR1L_REQUIRE(plan != nullptr, "plan is null");
+    const LatticeWork& lw = plan->lw;
+    if (L) *L = lw.L;
+    if (M_out)
+      for (int l = 0; l < lw.L; ++l) M_out[l] = lw.Mh[l];
+    if (z_out)
+      for (size_t i = 0; i < lw.zh.size(); ++i) z_out[i] = lw.zh[i];
+    if (nodes) *nodes = 1 - lw.L + lw.sumM_all;
+    if (sum_M) *sum_M = lw.sumM_all;
+    if (n_uncovered) *n_uncovered = lw.n_uncovered;
+  });
+}
+
+extern "C" int mr1l_plan_masks(const mr1l_plan_t* plan, uint64_t* masks, uint32_t* res) {
+  return guarded([&] {
+    MR1L_REQUIRE(plan != nullptr, "plan is null");
+    const LatticeWork& lw = plan->lw;
+    if (masks)
+      MR1L_CUDA(cudaMemcpy(masks, lw.umask.get(), plan->nI * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (res) {
+      MR1L_CUDA(cudaMemcpy(res, lw.pre_res.get(), (size_t)lw.L * plan->nI * sizeof(uint32_t),
+                           cudaMemcpyDeviceToHost));
+    }
+  });
+}
+
+extern "C" void mr1l_destroy(mr1l_plan_t* plan) { delete plan; }
+
+extern "C" int mr1l_reconstruct(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* stream) {
+  return guarded([&] {
+    MR1L_REQUIRE(plan != nullptr, "plan is null");
+    MR1L_REQUIRE(nrhs >= 0 && nrhs <= 65535 / 64, "nrhs out of range");
+    if (nrhs == 0) return;
+    MR1L_REQUIRE(y != nullptr && c != nullptr, "null array");
+    MR1L_REQUIRE(((uintptr_t)y & 15) == 0 && ((uintptr_t)c & 15) == 0, "arrays must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    LatticeWork& lw = plan->lw;
+    const int64_t sumM = lw.sumM;
+    plan->C.reserve((size_t)nrhs * sumM);
+    plan->work.reserve((size_t)nrhs * lw.Luse * lw.geom.P);
+    BlueIO io{};
+    io.in = (const cplx*)y;
+    io.in_stride = sumM;
+    io.out = plan->C.get();
+    io.out_stride = sumM;
+    io.work = plan->work.get();
+    blue_run(lw.geom, io, kModeRecon, nrhs, s);
+    gather(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, plan->C.get(), sumM, nrhs, (cplx*)c, plan->nI,
+           nullptr, nullptr, s);
+  });
+}
+
+extern "C" int mr1l_evaluate(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode, void* stream) {
+  return guarded([&] {
+    MR1L_REQUIRE(plan != nullptr, "plan is null");
+    MR1L_REQUIRE(mode == MR1L_EVAL || mode == MR1L_ADJOINT, "mode must be MR1L_EVAL or MR1L_ADJOINT");
+    MR1L_REQUIRE(nrhs >= 0 && nrhs <= 65535 / 64, "nrhs out of range");
+    if (nrhs == 0) return;
+    MR1L_REQUIRE(y != nullptr && c != nullptr, "null array");
+    MR1L_REQUIRE(((uintptr_t)y & 15) == 0 && ((uintptr_t)c & 15) == 0, "arrays must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    LatticeWork& lw = plan->lw;
+    const int64_t sumM = lw.sumM;
+    plan->bins.reserve((size_t)nrhs * sumM);
+    plan->work.reserve((size_t)nrhs * lw.Luse * lw.geom.P);
+    MR1L_CUDA(cudaMemsetAsync(plan->bins.get(), 0, (size_t)nrhs * sumM * sizeof(cplx), s));
+    scatter(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, (const cplx*)c, plan->nI, nrhs,
+            mode == MR1L_ADJOINT, plan->bins.get(), sumM, s);
+    BlueIO io{};
+    io.in = plan->bins.get();
+    io.in_stride = sumM;
+    io.out = (cplx*)y;
+    io.out_stride = sumM;
+    io.work = plan->work.get();
+    blue_run(lw.geom, io, kModeEval, nrhs, s);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 3
+// ---------------------------------------------------------------------------
+namespace mr1l {
+
+struct SfftRun {
+  sfft_params P;
+  sfft_sampler S;
+  cudaStream_t s;
+  int K;
+  double theta2;
+  int rel;
+  sfft_stats stats{};
+  // planted signal on the device
+  DevBuf<int32_t> freqs;
+  DevBuf<cplx> coeffs;
+  // candidate prefix (device + host mirror) and last list
+  DevBuf<int32_t> pre, pre_next, last;
+  std::vector<int32_t> pre_h;
+  int64_t np = 0;
+  int tp = 0;
+  LatticeWork lw;
+  DevBuf<double> anchors;
+  DevBuf<cplx> y, C, bins, work, pvals, coef_out;
+  DevBuf<uint64_t> keys, keymax;
+  DevBuf<SelectState> sel;
+  DevBuf<uint8_t> flags, line_sel;
+  DevBuf<int64_t> counts;
+  DevBuf<cplx> line_y, line_bins;
+  std::vector<cudaEvent_t> ev;
+  std::vector<double> final_coeffs;
+
+  ~SfftRun() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+
+  void ev_record() {
+    cudaEvent_t e;
+    MR1L_CUDA(cudaEventCreate(&e));
+    MR1L_CUDA(cudaEventRecord(e, s));
+    ev.push_back(e);
+  }
+
+  std::vector<double> anchor_rows(uint32_t purpose, int t, int rep0, int count) {
+    std::vector<double> a((size_t)count * P.d);
+    for (int i = 0; i < count; ++i)
+      for (int j = 0; j < P.d; ++j)
+        a[(size_t)i * P.d + j] =
+            u64_to_unit(philox_u64(P.seed, purpose, (uint32_t)t, (uint32_t)j, 0u, (uint32_t)(rep0 + i)).a);
+    return a;
+  }
+
+  // Steps 1 / 2a: I^(t) from r random lines.
+  std::vector<int32_t> detect(int t) {
+    const int r = P.r;
+    std::vector<double> a = anchor_rows(kAnchorLine, t, 0, r);
+    anchors.reserve(a.size());
+    MR1L_CUDA(cudaMemcpyAsync(anchors.get(), a.data(), a.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    line_y.reserve((size_t)r * K);
+    line_bins.reserve((size_t)r * K);
+    line_sel.reserve(K);
+    ev_record();
+    if (S.fn) {
+      for (int i = 0; i < r; ++i) {
+        sfft_request q{};
+        q.kind = SFFT_REQ_LINE;
+        q.t = t;
+        q.rep = i;
+        q.d = P.d;
+        q.anchors = a.data() + (size_t)i * P.d;
+        q.K = K;
+        int rc = S.fn(S.user, &q, line_y.get() + (size_t)i * K, s);
+        if (rc != 0) throw Error(MR1L_E_SAMPLER, "sampler callback failed (line request)");
+      }
+    } else {
+      planted_lines(freqs.get(), coeffs.get(), S.s, P.d, t, K, anchors.get(), r, S.sigma / std::sqrt(2.0),
+                    S.noise_seed, 0, line_bins.get(), line_y.get(), s);
+    }
+    ev_record();
+    MR1L_CUDA(cudaMemsetAsync(line_sel.get(), 0, K, s));
+    detect_lines(line_y.get(), r, P.N, P.s_local, theta2, rel, line_sel.get(), s);
+    std::vector<uint8_t> h(K);
+    MR1L_CUDA(cudaMemcpyAsync(h.data(), line_sel.get(), K, cudaMemcpyDeviceToHost, s));
+    MR1L_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> out;
+    for (int a2 = 0; a2 < K; ++a2)
+      if (h[a2]) out.push_back(a2 - P.N);
+    return out;
+  }
+
+  // One group of repetitions [rep0, rep0 + nrep): sample, reconstruct, select.
+  void passes(const CandSet& J, int t, int rep0, int nrep, int64_t cap, int last_pass) {
+    const int64_t n = J.n();
+    const int64_t sumM = lw.sumM;
+    std::vector<double> a = anchor_rows(kAnchorLattice, t, rep0, nrep);
+    anchors.reserve(a.size());
+    MR1L_CUDA(cudaMemcpyAsync(anchors.get(), a.data(), a.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    y.reserve((size_t)nrep * sumM);
+    C.reserve((size_t)nrep * sumM);
+    work.reserve((size_t)nrep * lw.Luse * lw.geom.P);
+    ev_record();
+    if (S.fn) {
+      for (int i = 0; i < nrep; ++i) {
+        sfft_request q{};
+        q.kind = SFFT_REQ_LATTICE;
+        q.t = t;
+        q.rep = rep0 + i;
+        q.d = P.d;
+        q.anchors = a.data() + (size_t)i * P.d;
+        q.L = lw.Luse;
+        std::vector<int64_t> Ml(lw.Mh.begin(), lw.Mh.begin() + lw.Luse);
+        q.M = Ml.data();
+        q.z = lw.zh.data();
+        q.sum_M = sumM;
+        int rc = S.fn(S.user, &q, y.get() + (size_t)i * sumM, s);
+        if (rc != 0) throw Error(MR1L_E_SAMPLER, "sampler callback failed (lattice request)");
+      }
+    } else {
+      bins.reserve((size_t)nrep * sumM);
+      MR1L_CUDA(cudaMemsetAsync(bins.get(), 0, (size_t)nrep * sumM * sizeof(cplx), s));
+      planted_lattice_bins(freqs.get(), coeffs.get(), S.s, P.d, t, anchors.get(), nrep, lw.dev(), lw.Luse, lw.geom,
+                           bins.get(), sumM, s);
+      BlueIO io{};
+      io.in = bins.get();
+      io.in_stride = sumM;
+      io.out = y.get();
+      io.out_stride = sumM;
+      io.work = work.get();
+      io.noise_scale = S.sigma > 0 ? S.sigma / std::sqrt(2.0) : 0.0;
+      io.noise_seed = S.noise_seed;
+      io.noise_t = t;
+      io.noise_rep = rep0;
+      io.noise_rep_per_rhs = 1;
+      blue_run(lw.geom, io, kModeEval, nrep, s);
+    }
+    ev_record();
+    BlueIO io{};
+    io.in = y.get();
+    io.in_stride = sumM;
+    io.out = C.get();
+    io.out_stride = sumM;
+    io.work = work.get();
+    blue_run(lw.geom, io, kModeRecon, nrep, s);
+    pvals.reserve((size_t)nrep * n);
+    keys.reserve((size_t)nrep * n);
+    keymax.reserve(nrep);
+    sel.reserve(nrep);
+    MR1L_CUDA(cudaMemsetAsync(keymax.get(), 0, nrep * sizeof(uint64_t), s));
+    gather(J, lw.dev(), lw.Luse, lw.umask.get(), lw.geom, C.get(), sumM, nrep, pvals.get(), n, keys.get(),
+           keymax.get(), s);
+    select_topk(keys.get(), n, nrep, keymax.get(), theta2, rel, cap, sel.get(), flags.get(), s);
+    (void)last_pass;
+  }
+
+  void run(sfft_result* res) {
+    auto t0 = std::chrono::steady_clock::now();
+    const int d = P.d;
+    K = 2 * P.N + 1;
+    theta2 = P.theta * P.theta;
+    rel = P.theta_mode == SFFT_THETA_REL;
+    if (!S.fn) {
+      freqs.reserve(std::max<int64_t>(S.s * d, 1));
+      coeffs.reserve(std::max<int64_t>(S.s, 1));
+      if (S.s) {
+        MR1L_CUDA(cudaMemcpyAsync(freqs.get(), S.freqs, S.s * d * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        MR1L_CUDA(cudaMemcpyAsync(coeffs.get(), S.coeffs, S.s * sizeof(cplx), cudaMemcpyHostToDevice, s));
+      }
+    }
+    // step 1
+    std::vector<int32_t> I1 = detect(1);
+    stats.samples += (int64_t)P.r * K;
+    pre_h.assign(I1.begin(), I1.end());
+    np = (int64_t)I1.size();
+    tp = 1;
+    std::vector<cplx> coef_h;
+    // step 2
+    for (int t = 2; t <= d; ++t) {
+      std::vector<int32_t> It = detect(t);
+      sfft_step_stats& st = stats.steps[stats.n_steps++];
+      st.t = t;
+      st.n_line = (int)It.size();
+      st.samples = (int64_t)P.r * K;
+      const int rt = t < d ? P.r : 1;
+      const int64_t cap = t < d ? P.s_local : P.s;
+      const int64_t n = np * (int64_t)It.size();
+      st.n_cand = n;
+      if (n == 0) {
+        np = 0;
+        tp = t;
+        pre_h.clear();
+        stats.samples += st.samples;
+        st.covered = 1;
+        continue;
+      }
+      pre.reserve(np * tp);
+      MR1L_CUDA(cudaMemcpyAsync(pre.get(), pre_h.data(), np * tp * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      last.reserve(It.size());
+      MR1L_CUDA(cudaMemcpyAsync(last.get(), It.data(), It.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      CandSet J;
+      J.tp = tp;
+      J.t = t;
+      J.np = np;
+      J.nq = (int64_t)It.size();
+      J.pre = pre.get();
+      J.last = last.get();
+      // step 2b: Algorithm 1, up to b searches
+      int Lmax;
+      double lam;
+      lmax_lambda(n, 2.0, 0.5, Lmax, lam);
+      MR1L_REQUIRE(Lmax >= 1 && Lmax <= 64, "Lmax out of range");
+      HostRows rows{pre_h.data(), tp, np, It.data(), (int64_t)It.size()};
+      std::vector<int> primes = prime_set(rows, lam, Lmax);
+      std::vector<int64_t> zs;
+      int attempts = 0;
+      for (int a = 0; a < P.b; ++a) {
+        draw_z(P.seed, t, a, primes, zs);
+        lw.load(J, primes, zs, t, s);
+        attempts = a + 1;
+        if (lw.n_uncovered == 0) break;
+      }
+      const int covered = lw.n_uncovered == 0;
+      const int Luse = covered ? lw.Lneed : Lmax;
+      lw.tables(Luse, s);
+      st.L = Luse;
+      st.attempts = attempts;
+      st.covered = covered;
+      st.sum_M = lw.sumM;
+      flags.reserve(n);
+      MR1L_CUDA(cudaMemsetAsync(flags.get(), 0, n, s));
+      // steps 2c-2e
+      if (P.batch_reps) {
+        passes(J, t, 0, rt, cap, 1);
+      } else {
+        for (int i = 0; i < rt; ++i) passes(J, t, i, 1, cap, i == rt - 1);
+      }
+      st.samples += (int64_t)rt * (1 - Luse + lw.sumM);
+      stats.samples += st.samples;
+      // compaction: next prefix I^(1..t) (and the coefficients at t = d)
+      pre_next.reserve(n * t);
+      counts.reserve(cdiv(n, 1024) + 1);
+      if (t == d) coef_out.reserve(n);
+      int64_t cnt = compact(J, flags.get(), pre_next.get(), t == d ? pvals.get() : nullptr,
+                            t == d ? coef_out.get() : nullptr, counts.get(), (int64_t)counts.n, s);
+      np = cnt;
+      tp = t;
+      pre_h.resize(np * tp);
+      if (np)
+        MR1L_CUDA(cudaMemcpyAsync(pre_h.data(), pre_next.get(), np * tp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      if (t == d) {
+        coef_h.resize(np);
+        if (np) MR1L_CUDA(cudaMemcpyAsync(coef_h.data(), coef_out.get(), np * sizeof(cplx), cudaMemcpyDeviceToHost, s));
+      }
+      MR1L_CUDA(cudaStreamSynchronize(s));
+      st.n_detected = np;
+    }
+    MR1L_CUDA(cudaStreamSynchronize(s));
+    double samp = 0.0;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      float ms = 0.f;
+      MR1L_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      samp += ms;
+    }
+    stats.ms_sampling = samp;
+    stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    res->n = np;
+    res->d = d;
+    res->freqs = (int32_t*)std::malloc(std::max<int64_t>(np * d, 1) * sizeof(int32_t));
+    res->coeffs = (double*)std::malloc(std::max<int64_t>(np, 1) * 2 * sizeof(double));
+    if (!res->freqs || !res->coeffs) throw std::bad_alloc();
+    if (np) {
+      std::memcpy(res->freqs, pre_h.data(), np * d * sizeof(int32_t));
+      std::memcpy(res->coeffs, coef_h.data(), np * sizeof(cplx));
+    }
+    res->stats = stats;
+  }
+};
+
+}  // namespace mr1l
+
+extern "C" int sfft_dimincr(const sfft_params* params, const sfft_sampler* sampler, void* stream, sfft_result** out) {
+  return guarded([&] {
+    MR1L_REQUIRE(params && sampler && out, "null argument");
+    *out = nullptr;
+    const sfft_params& P = *params;
+    MR1L_REQUIRE(P.d >= 2 && P.d <= SFFT_MAX_STEPS, "d must be in [2, 256]");
+    MR1L_REQUIRE(P.N >= 1 && P.N <= 2048, "N must be in [1, 2048]");
+    MR1L_REQUIRE(P.s >= 1 && P.s_local >= 1, "s and s_local must be >= 1");
+    MR1L_REQUIRE(P.r >= 1 && P.r <= 4096, "r must be in [1, 4096]");
+    MR1L_REQUIRE(P.b >= 1, "b must be >= 1");
+    MR1L_REQUIRE(P.theta >= 0.0 && std::isfinite(P.theta), "theta must be finite and >= 0");
+    MR1L_REQUIRE(P.theta_mode == SFFT_THETA_ABS || P.theta_mode == SFFT_THETA_REL, "bad theta_mode");
+    if (!sampler->fn) {
+      MR1L_REQUIRE(sampler->s >= 0, "planted s must be >= 0");
+      MR1L_REQUIRE(sampler->s == 0 || (sampler->freqs && sampler->coeffs), "planted arrays are null");
+      MR1L_REQUIRE(sampler->sigma >= 0.0, "sigma must be >= 0");
+      for (int64_t i = 0; i < sampler->s * P.d; ++i)
+        MR1L_REQUIRE(sampler->freqs[i] > -32768 && sampler->freqs[i] < 32768, "|h_j| must be < 2^15");
+    }
+    std::unique_ptr<SfftRun> run(new SfftRun());
+    run->P = P;
+    run->S = *sampler;
+    run->s = (cudaStream_t)stream;
+    std::unique_ptr<sfft_result> res(new sfft_result());
+    std::memset(res.get(), 0, sizeof(sfft_result));
+    run->run(res.get());
+    *out = res.release();
+  });
+}
+
+extern "C" void sfft_free(sfft_result* res) {
+  if (!res) return;
+  std::free(res->freqs);
+  std::free(res->coeffs);
+  delete res;
+}

@@ -1,0 +1,472 @@
+// Bluestein prime-length DFTs over power-of-two FP64 FFTs.
+//
+// A length-M DFT X[r] = sum_j x[j] exp(-2 pi i j r / M) (Algorithm 2, one
+// lattice) is rewritten with j r = (j^2 + r^2 - (r - j)^2) / 2 as
+//   X[r] = w[r] * sum_j (x[j] w[j]) conj(w[r - j]),   w[n] = exp(-pi i n^2 / M),
+// a linear convolution evaluated by power-of-two FFTs of length P >= 2M - 1.
+// The chirp phase uses n^2 mod 2M reduced in exact integers.
+//
+// On GB300 the FP64 pipe (about 2 FMA per clock per SM) bounds these
+// transforms, so the kernels read chirps, filters and twiddles from tables
+// instead of recomputing them, and never spend FP64 work on index math.
+//
+// Structure: P <= 4096 runs in one CTA per transform (everything in shared
+// memory).  Larger P uses the 4-step split P = P1 * P2 without transposes:
+//   pass 1 (columns): FFT_P1 over n1 of x[n1 P2 + n2], times w_P^(n2 k1),
+//                     stored at k1 P2 + n2;
+//   pass 2 (rows):    FFT_P2 over n2 (giving X[k1 + P1 k2] at k1 P2 + k2),
+//                     times the filter spectrum (stored in the same order),
+//                     inverse FFT_P2, times w_P^(-n2 k1);
+//   pass 3 (columns): inverse FFT_P1 over k1, natural order x[n1 P2 + n2].
+// Each sub-FFT is a mixed-radix (8, 4, 2) Stockham autosort FFT in shared
+// memory (Govindaraju et al., SC'08 formulation).
+#include <map>
+#include <mutex>
+
+#include "fft.cuh"
+
+namespace mr1l {
+
+// ---------------------------------------------------------------------------
+// Register DFTs of size 2, 4, 8 (forward: exp(-2 pi i / R); INV: conjugate).
+// ---------------------------------------------------------------------------
+template <int R, bool INV>
+struct RegDft;
+
+template <bool INV>
+struct RegDft<2, INV> {
+  static __device__ __forceinline__ void run(cplx* v) {
+    cplx a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <bool INV>
+struct RegDft<4, INV> {
+  static __device__ __forceinline__ void run(cplx* v) {
+    cplx t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    cplx t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+template <bool INV>
+struct RegDft<8, INV> {
+  static __device__ __forceinline__ void run(cplx* v) {
+    const double h = 0.70710678118654752440;  // 1/sqrt(2)
+    cplx e[4] = {v[0], v[2], v[4], v[6]};
+    cplx o[4] = {v[1], v[3], v[5], v[7]};
+    RegDft<4, INV>::run(e);
+    RegDft<4, INV>::run(o);
+    // o1 *= w8, o2 *= w8^2 = -+i, o3 *= w8^3
+    cplx a = o[1], c = o[3];
+    if (!INV) {
+      o[1] = cmake((a.x + a.y) * h, (a.y - a.x) * h);
+      o[3] = cmake((c.y - c.x) * h, -(c.x + c.y) * h);
+    } else {
+      o[1] = cmake((a.x - a.y) * h, (a.x + a.y) * h);
+      o[3] = cmake(-(c.x + c.y) * h, (c.x - c.y) * h);
+    }
+    o[2] = mul_mi<INV>(o[2]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = cadd(e[k], o[k]);
+      v[k + 4] = csub(e[k], o[k]);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// One Stockham stage of radix R over nseq sequences of length n in shared
+// memory; element i of sequence b sits at s[b * bs + i * is].  Every thread
+// owns 8 values (8/R butterflies); blockDim.x * 8 == nseq * n (or more
+// threads than needed, which idle).
+//   COLS: sequence index fastest across threads (column tiles, bs == 1)
+//   else: element index fastest (row tiles, is == 1)
+// ---------------------------------------------------------------------------
+template <int R, bool INV, bool COLS>
+__device__ __forceinline__ void stockham_stage(cplx* s, int n, int lognb, int Ns, int nseq, int bs,
+                                               int is, const cplx* twn_n) {
+  constexpr int CNT = 8 / R;
+  const int nb = n / R;
+  const int total = nseq * nb;
+  cplx v[CNT][R];
+  int base[CNT];
+  bool act[CNT];
+#pragma unroll
+  for (int c = 0; c < CNT; ++c) {
+    int idx = threadIdx.x + c * blockDim.x;
+    act[c] = idx < total;
+    int b, j;
+    if (COLS) {
+      b = idx % nseq;
+      j = idx / nseq;
+    } else {
+      j = idx & (nb - 1);
+      b = idx >> lognb;
+    }
+    int k = j & (Ns - 1);
+    base[c] = b * bs + ((j - k) * R + k) * is;
+    if (act[c]) {
+      const cplx* src = s + b * bs + j * is;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[c][r] = src[r * nb * is];
+      if (Ns > 1) {
+        int step = k * (n / (Ns * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          cplx w = twn_n[r * step];
+          v[c][r] = INV ? cmulc(v[c][r], w) : cmul(v[c][r], w);
+        }
+      }
+      RegDft<R, INV>::run(v[c]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < CNT; ++c) {
+    if (act[c]) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[base[c] + r * Ns * is] = v[c][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full in-smem FFT of length n = 2^logn (radix-8 stages, then one radix-4 or
+// radix-2 stage).  Natural order in and out.
+template <bool INV, bool COLS>
+__device__ __forceinline__ void smem_fft(cplx* s, int n, int logn, int nseq, int bs, int is,
+                                         const cplx* twn) {
+  const cplx* twn_n = twn + n;
+  int Ns = 1, rem = logn;
+  while (rem >= 3) {
+    stockham_stage<8, INV, COLS>(s, n, logn - 3, Ns, nseq, bs, is, twn_n);
+    Ns <<= 3;
+    rem -= 3;
+  }
+  if (rem == 2) stockham_stage<4, INV, COLS>(s, n, logn - 2, Ns, nseq, bs, is, twn_n);
+  if (rem == 1) stockham_stage<2, INV, COLS>(s, n, logn - 1, Ns, nseq, bs, is, twn_n);
+}
+
+// ---------------------------------------------------------------------------
+// Sources and sinks
+// ---------------------------------------------------------------------------
+template <int MODE>
+__device__ __forceinline__ cplx load_input(const BlueGeom& g, const BlueIO& io, int l, int h, int M,
+                                           int64_t off, int64_t n) {
+  if (MODE == kModeFilter) {
+    if (n < M) return cconj(g.w[off + n]);
+    if (n > g.P - M) return cconj(g.w[off + (g.P - n)]);
+    return cmake(0.0, 0.0);
+  }
+  if (n >= M) return cmake(0.0, 0.0);
+  cplx x = io.in[h * io.in_stride + off + n];
+  if (MODE == kModeRecon) return cmul(x, g.ws[off + n]);
+  return cmul(cconj(x), g.w[off + n]);
+}
+
+__device__ __forceinline__ cplx lattice_noise(uint64_t seed, int t, int rep, int l, int64_t j, double scale) {
+  U64Pair u = philox_u64(seed, kNoiseLattice, (uint32_t)t, (uint32_t)j, j == 0 ? 0u : (uint32_t)l,
+                         (uint32_t)rep);
+  double u1 = ((double)(u.a >> 11) + 1.0) * 0x1.0p-53;
+  double u2 = (double)(u.b >> 11) * 0x1.0p-53;
+  double R = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  return cmake(scale * (R * cs), scale * (R * sn));
+}
+
+template <int MODE>
+__device__ __forceinline__ void store_output(const BlueGeom& g, const BlueIO& io, int l, int h, int64_t off,
+                                             int64_t n, cplx v) {
+  if (MODE == kModeRecon) {
+    io.out[h * io.out_stride + off + n] = v;
+  } else {
+    cplx y = cconj(cmul(g.w[off + n], v));
+    if (io.noise_scale != 0.0) {
+      cplx e = lattice_noise(io.noise_seed, io.noise_t, io.noise_rep + h * io.noise_rep_per_rhs, l, n,
+                             io.noise_scale);
+      y = cadd(y, e);
+    }
+    io.out[h * io.out_stride + off + n] = y;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// P <= 4096: the whole convolution in one CTA.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) {
+  extern __shared__ cplx sm[];
+  const int gi = blockIdx.x;
+  const int l = gi % g.L, h = gi / g.L;
+  const int P = g.P, M = g.M[l];
+  const int64_t off = g.off[l];
+  for (int n = threadIdx.x; n < P; n += blockDim.x) sm[n] = load_input<MODE>(g, io, l, h, M, off, n);
+  __syncthreads();
+  smem_fft<false, false>(sm, P, g.logP, 1, 0, 1, g.twn);
+  cplx* Bh = g.Bh + (int64_t)l * P;
+  if (MODE == kModeFilter) {
+    const double sc = 1.0 / (double)P;  // exact: P is a power of two
+    for (int n = threadIdx.x; n < P; n += blockDim.x) Bh[n] = cmake(sm[n].x * sc, sm[n].y * sc);
+    return;
+  }
+  for (int n = threadIdx.x; n < P; n += blockDim.x) sm[n] = cmul(sm[n], Bh[n]);
+  __syncthreads();
+  smem_fft<true, false>(sm, P, g.logP, 1, 0, 1, g.twn);
+  for (int n = threadIdx.x; n < M; n += blockDim.x) store_output<MODE>(g, io, l, h, off, n, sm[n]);
+}
+
+// ---------------------------------------------------------------------------
+// 4-step passes
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int col_tile(int P1) {
+  int cb = 4096 / P1;
+  return cb > 16 ? 16 : (cb < 1 ? 1 : cb);
+}
+__host__ __device__ __forceinline__ int row_tile(int P2) {
+  int rb = 4096 / P2;
+  return rb < 1 ? 1 : rb;
+}
+
+// Pass 1: columns, forward, with the 4-step twiddle.
+template <int MODE>
+__global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io) {
+  extern __shared__ cplx sm[];
+  const int gi = blockIdx.y;
+  const int l = gi % g.L, h = gi / g.L;
+  const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1);
+  const int logP1 = g.logP - ilog2_pow2(P2);
+  const int M = g.M[l];
+  const int64_t off = g.off[l];
+  const int n2_0 = blockIdx.x * CB;
+  for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
+    int i = e / CB, b = e - i * CB;
+    sm[e] = load_input<MODE>(g, io, l, h, M, off, (int64_t)i * P2 + n2_0 + b);
+  }
+  __syncthreads();
+  smem_fft<false, true>(sm, P1, logP1, CB, 1, CB, g.twn);
+  cplx* work = io.work + (int64_t)gi * P;
+  for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
+    int k1 = e / CB, b = e - k1 * CB;
+    int n2 = n2_0 + b;
+    cplx w = g.tw[((int64_t)n2 * k1) & (P - 1)];
+    work[(int64_t)k1 * P2 + n2] = cmul(sm[e], w);
+  }
+}
+
+// Pass 2: rows.  FILTER: forward FFT scaled by 1/P into Bh.  Otherwise forward
+// FFT, times Bh, inverse FFT, times conj(w_P^(n2 k1)).
+template <bool FILTER>
+__global__ void __launch_bounds__(512) blue_row_kernel(BlueGeom g, BlueIO io) {
+  extern __shared__ cplx sm[];
+  const int gi = blockIdx.y;
+  const int l = gi % g.L;
+  const int P = g.P, P2 = g.P2, RB = row_tile(P2);
+  const int logP2 = ilog2_pow2(P2);
+  const int k1_0 = blockIdx.x * RB;
+  cplx* work = io.work + (int64_t)gi * P + (int64_t)k1_0 * P2;
+  for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = work[e];
+  __syncthreads();
+  smem_fft<false, false>(sm, P2, logP2, RB, P2, 1, g.twn);
+  cplx* Bh = g.Bh + (int64_t)l * P + (int64_t)k1_0 * P2;
+  if (FILTER) {
+    const double sc = 1.0 / (double)P;
+    for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) Bh[e] = cmake(sm[e].x * sc, sm[e].y * sc);
+    return;
+  }
+  for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = cmul(sm[e], Bh[e]);
+  __syncthreads();
+  smem_fft<true, false>(sm, P2, logP2, RB, P2, 1, g.twn);
+  for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) {
+    int b = e / P2, n2 = e - b * P2;
+    int k1 = k1_0 + b;
+    cplx w = g.tw[((int64_t)n2 * k1) & (P - 1)];
+    work[e] = cmulc(sm[e], w);
+  }
+}
+
+// Pass 3: columns, inverse; natural-order output n = n1 P2 + n2 for n < M.
+template <int MODE>
+__global__ void __launch_bounds__(512) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
+  extern __shared__ cplx sm[];
+  const int gi = blockIdx.y;
+  const int l = gi % g.L, h = gi / g.L;
+  const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1);
+  const int logP1 = g.logP - ilog2_pow2(P2);
+  const int M = g.M[l];
+  const int64_t off = g.off[l];
+  const int n2_0 = blockIdx.x * CB;
+  const cplx* work = io.work + (int64_t)gi * P;
+  for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
+    int k1 = e / CB, b = e - k1 * CB;
+    sm[e] = work[(int64_t)k1 * P2 + n2_0 + b];
+  }
+  __syncthreads();
+  smem_fft<true, true>(sm, P1, logP1, CB, 1, CB, g.twn);
+  for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
+    int n1 = e / CB, b = e - n1 * CB;
+    int64_t n = (int64_t)n1 * P2 + n2_0 + b;
+    if (n < M) store_output<MODE>(g, io, l, h, off, n, sm[e]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tables
+// ---------------------------------------------------------------------------
+__global__ void twiddle_kernel(cplx* tw, int64_t P) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= P) return;
+  double s, c;
+  sincospi(2.0 * (double)e / (double)P, &s, &c);  // 2e/P is exact
+  tw[e] = cmake(c, -s);
+}
+
+__global__ void small_twiddle_kernel(cplx* tw) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;  // [0, 8192)
+  if (i < 2 || i >= 8192) return;
+  int n = 1 << (31 - __clz(i));  // table of size n sits at [n, 2n)
+  int e = i - n;
+  double s, c;
+  sincospi(2.0 * (double)e / (double)n, &s, &c);
+  tw[i] = cmake(c, -s);
+}
+
+__global__ void chirp_kernel(cplx* w, cplx* ws, const int64_t* off, const int* Ms, int L) {
+  int l = blockIdx.y;
+  int M = Ms[l];
+  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= M) return;
+  uint64_t q = ((uint64_t)n * (uint64_t)n) % (uint64_t)(2 * (int64_t)M);  // exact n^2 mod 2M
+  double s, c;
+  sincospi((double)q / (double)M, &s, &c);
+  cplx v = cmake(c, -s);  // exp(-pi i q / M)
+  w[off[l] + n] = v;
+  double inv = 1.0 / (double)M;
+  ws[off[l] + n] = cmake(c * inv, -s * inv);
+}
+
+namespace {
+std::mutex g_tw_mu;
+std::map<std::pair<int, int>, cplx*> g_tw;  // (device, logP) -> table
+std::map<int, cplx*> g_twn;                 // device -> small tables
+}  // namespace
+
+const cplx* twiddle_table(int logP, cudaStream_t s) {
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto key = std::make_pair(dev, logP);
+  auto it = g_tw.find(key);
+  if (it != g_tw.end()) return it->second;
+  int64_t P = int64_t(1) << logP;
+  cplx* p = nullptr;
+  MR1L_CUDA(cudaMalloc(&p, P * sizeof(cplx)));
+  twiddle_kernel<<<cdiv(P, 256), 256, 0, s>>>(p, P);
+  MR1L_CHECK_LAUNCH("twiddle_kernel");
+  MR1L_CUDA(cudaStreamSynchronize(s));
+  g_tw[key] = p;
+  return p;
+}
+
+const cplx* small_twiddles(cudaStream_t s) {
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto it = g_twn.find(dev);
+  if (it != g_twn.end()) return it->second;
+  cplx* p = nullptr;
+  MR1L_CUDA(cudaMalloc(&p, 8192 * sizeof(cplx)));
+  MR1L_CUDA(cudaMemsetAsync(p, 0, 8192 * sizeof(cplx), s));
+  small_twiddle_kernel<<<32, 256, 0, s>>>(p);
+  MR1L_CHECK_LAUNCH("small_twiddle_kernel");
+  MR1L_CUDA(cudaStreamSynchronize(s));
+  g_twn[dev] = p;
+  return p;
+}
+
+void blue_split(BlueGeom& g, int logP) {
+  MR1L_REQUIRE(logP >= 1 && logP <= 24, "Bluestein length out of range (2 .. 2^24)");
+  g.logP = logP;
+  g.P = 1 << logP;
+  if (logP <= kSmallLog) {
+    g.P1 = 1;
+    g.P2 = g.P;
+  } else {
+    int l1 = logP / 2;
+    g.P1 = 1 << l1;
+    g.P2 = 1 << (logP - l1);
+  }
+}
+
+void chirp_tables(const BlueGeom& g, int64_t max_M, cudaStream_t s) {
+  dim3 grid(cdiv(max_M, 256), g.L);
+  chirp_kernel<<<grid, 256, 0, s>>>(const_cast<cplx*>(g.w), const_cast<cplx*>(g.ws), g.off, g.M, g.L);
+  MR1L_CHECK_LAUNCH("chirp_kernel");
+}
+
+template <typename K>
+static void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) MR1L_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+static int threads_for(int elems) {
+  int t = elems / 8;
+  if (t < 32) t = 32;
+  return t;
+}
+
+template <int MODE>
+static void launch_first_last(const BlueGeom& g, const BlueIO& io, int ntrans, cudaStream_t s) {
+  if (g.logP <= kSmallLog) {
+    size_t smem = (size_t)g.P * sizeof(cplx);
+    set_smem(blue_small_kernel<MODE>, smem);
+    blue_small_kernel<MODE><<<ntrans, threads_for(g.P), smem, s>>>(g, io);
+    MR1L_CHECK_LAUNCH("blue_small_kernel");
+    return;
+  }
+  int CB = col_tile(g.P1), RB = row_tile(g.P2);
+  size_t smem_c = (size_t)g.P1 * CB * sizeof(cplx);
+  size_t smem_r = (size_t)RB * g.P2 * sizeof(cplx);
+  dim3 gc(g.P2 / CB, ntrans), gr(g.P1 / RB, ntrans);
+  set_smem(blue_col_fwd_kernel<MODE>, smem_c);
+  blue_col_fwd_kernel<MODE><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io);
+  MR1L_CHECK_LAUNCH("blue_col_fwd_kernel");
+  if (MODE == kModeFilter) {
+    set_smem(blue_row_kernel<true>, smem_r);
+    blue_row_kernel<true><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io);
+    MR1L_CHECK_LAUNCH("blue_row_kernel<filter>");
+    return;
+  }
+  set_smem(blue_row_kernel<false>, smem_r);
+  blue_row_kernel<false><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io);
+  MR1L_CHECK_LAUNCH("blue_row_kernel");
+  set_smem(blue_col_inv_kernel<MODE>, smem_c);
+  blue_col_inv_kernel<MODE><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io);
+  MR1L_CHECK_LAUNCH("blue_col_inv_kernel");
+}
+
+void blue_filter(const BlueGeom& g, cudaStream_t s) {
+  // the filter pass needs P complex of scratch per lattice: use Bh itself as
+  // the 4-step work buffer (pass 1 writes it, pass 2 overwrites it in place
+  // row by row; each row is read completely before it is written)
+  BlueIO io{};
+  io.work = g.Bh;
+  launch_first_last<kModeFilter>(g, io, g.L, s);
+}
+
+void blue_run(const BlueGeom& g, const BlueIO& io, int mode, int nrhs, cudaStream_t s) {
+  int ntrans = g.L * nrhs;
+  if (ntrans == 0) return;
+  if (mode == kModeRecon)
+    launch_first_last<kModeRecon>(g, io, ntrans, s);
+  else
+    launch_first_last<kModeEval>(g, io, ntrans, s);
+}
+
+}  // namespace mr1l

@@ -1,0 +1,61 @@
+// Batched prime-length DFTs by Bluestein convolution over power-of-two FP64
+// FFTs (the per-lattice DFT of Algorithm 2 and of the lattice evaluation).
+#pragma once
+
+#include "common.cuh"
+
+namespace mr1l {
+
+// Source/sink of the first and last pass of a Bluestein convolution.
+enum BlueMode : int {
+  kModeFilter = 0,  // input b[n] = conj(w[n]) (n < M), conj(w[P-n]) (n > P-M), else 0
+  kModeRecon = 1,   // input y[n] * w[n] / M, output raw convolution C[n] (n < M)
+  kModeEval = 2,    // input conj(B[n]) * w[n], output conj(w[n] C[n]) (+ noise)
+};
+
+// Per-transform geometry shared by every pass of one batched launch.
+struct BlueGeom {
+  int L;            // lattices (transform g has lattice g % L, right-hand side g / L)
+  int P, logP;      // power-of-two convolution length, P >= 2 max M - 1
+  int P1, P2;       // 4-step split (P1 * P2 == P) when logP > kSmallLog
+  const int64_t* off;   // device [L]: offset of lattice l in per-lattice arrays
+  const int* M;         // device [L]: lattice sizes
+  const cplx* w;        // device [sum M]: chirp exp(-pi i n^2 / M)
+  const cplx* ws;       // device [sum M]: chirp / M
+  cplx* Bh;             // device [L][P]: filter spectrum FFT_P(b) / P (pass order)
+  const cplx* tw;       // device [P]: exp(-2 pi i e / P)
+  const cplx* twn;      // device [8192]: exp(-2 pi i e / n) for n = 2..4096 at offset n
+};
+
+struct BlueIO {
+  const cplx* in;       // RECON: samples y; EVAL: bins B (both [nrhs][sum M])
+  int64_t in_stride;    // per right-hand side
+  cplx* out;            // RECON: C; EVAL: y
+  int64_t out_stride;
+  cplx* work;           // [nrhs][L][P]
+  // optional complex Gaussian noise added in EVAL mode (Philox purpose 5)
+  double noise_scale;   // sigma / sqrt(2); 0 disables
+  uint64_t noise_seed;
+  int noise_t, noise_rep;
+  int noise_rep_per_rhs;  // rep index = noise_rep + rhs * noise_rep_per_rhs
+};
+
+constexpr int kSmallLog = 12;   // P <= 4096: one CTA holds the whole transform
+
+// Device-resident twiddle tables, cached per (device, P).
+const cplx* twiddle_table(int logP, cudaStream_t s);
+const cplx* small_twiddles(cudaStream_t s);
+
+// Fill geometry split for a given P.
+void blue_split(BlueGeom& g, int logP);
+
+// Build the filter spectra Bh for all L lattices (needs w).
+void blue_filter(const BlueGeom& g, cudaStream_t s);
+
+// Run nrhs * L Bluestein convolutions in mode kModeRecon or kModeEval.
+void blue_run(const BlueGeom& g, const BlueIO& io, int mode, int nrhs, cudaStream_t s);
+
+// Chirp tables w and ws for every lattice (w[n] = exp(-pi i (n^2 mod 2M)/M)).
+void chirp_tables(const BlueGeom& g, int64_t sum_M, cudaStream_t s);
+
+}  // namespace mr1l

@@ -1,0 +1,394 @@
+// Lattice-side kernels: residues, collision counting / coverage, the
+// averaged gather of Algorithm 2, scatter into lattice bins, the planted
+// sampler and the 1-D line detection of Algorithm 3.
+#include "ops.cuh"
+
+namespace mr1l {
+
+__device__ __forceinline__ uint32_t residue_of(const LatticeDev& lat, int64_t np, int64_t nq, int l,
+                                               int64_t p, int64_t q, uint32_t M) {
+  uint32_t r = lat.pre_res[(int64_t)l * np + p] + lat.last_res[(int64_t)l * nq + q];  // < 2^32
+  return r >= M ? r - M : r;
+}
+
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Residues k . z_l mod M_l (Section 2.1), exact in int64, canonical in [0, M).
+// ---------------------------------------------------------------------------
+__global__ void pre_res_kernel(CandSet J, LatticeDev lat) {
+  const int l = blockIdx.y;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= J.np) return;
+  const int64_t M = lat.M[l];
+  const int64_t* z = lat.z + (int64_t)l * lat.t;
+  const int32_t* k = J.pre + p * J.tp;
+  int64_t acc = 0;
+  for (int j = 0; j < J.tp; ++j) acc += (int64_t)k[j] * z[j];
+  acc %= M;
+  if (acc < 0) acc += M;
+  lat.pre_res[(int64_t)l * J.np + p] = (uint32_t)acc;
+}
+
+__global__ void last_res_kernel(CandSet J, LatticeDev lat) {
+  const int l = blockIdx.y;
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= J.nq) return;
+  int64_t acc = 0;
+  if (J.last) {
+    const int64_t M = lat.M[l];
+    acc = ((int64_t)J.last[q] * lat.z[(int64_t)l * lat.t + J.tp]) % M;
+    if (acc < 0) acc += M;
+  }
+  lat.last_res[(int64_t)l * J.nq + q] = (uint32_t)acc;
+}
+
+void residues(const CandSet& J, const LatticeDev& lat, cudaStream_t s) {
+  if (J.np > 0) {
+    pre_res_kernel<<<dim3(cdiv(J.np, 256), lat.L), 256, 0, s>>>(J, lat);
+    MR1L_CHECK_LAUNCH("pre_res_kernel");
+  }
+  last_res_kernel<<<dim3(cdiv(J.nq, 256), lat.L), 256, 0, s>>>(J, lat);
+  MR1L_CHECK_LAUNCH("last_res_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Collision counting: bucket state per residue in two bitmaps (seen once,
+// seen at least twice); order-free, so the result is deterministic.
+// ---------------------------------------------------------------------------
+__global__ void collide_kernel(CandSet J, LatticeDev lat, uint32_t* seen1, uint32_t* seen2,
+                               const int64_t* bm_off) {
+  const int l = blockIdx.y;
+  const int64_t n = J.np * J.nq;
+  const uint32_t M = (uint32_t)lat.M[l];
+  uint32_t* s1 = seen1 + bm_off[l];
+  uint32_t* s2 = seen2 + bm_off[l];
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = c / J.nq, q = c - p * J.nq;
+    uint32_t r = residue_of(lat, J.np, J.nq, l, p, q, M);
+    uint32_t bit = 1u << (r & 31);
+    uint32_t old = atomicOr(s1 + (r >> 5), bit);
+    if (old & bit) atomicOr(s2 + (r >> 5), bit);
+  }
+}
+
+// umask[c]: lattices in which c is collision-free; cover[0] = max over covered
+// c of (first covering lattice + 1); cover[1] = uncovered count.
+__global__ void cover_kernel(CandSet J, LatticeDev lat, const uint32_t* seen2, const int64_t* bm_off,
+                             uint64_t* umask, int* cover) {
+  const int64_t n = J.np * J.nq;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned need = 0, unc = 0;
+  if (c < n) {
+    int64_t p = c / J.nq, q = c - p * J.nq;
+    uint64_t m = 0;
+    for (int l = 0; l < lat.L; ++l) {
+      uint32_t r = residue_of(lat, J.np, J.nq, l, p, q, (uint32_t)lat.M[l]);
+      if (!(seen2[bm_off[l] + (r >> 5)] & (1u << (r & 31)))) m |= (uint64_t)1 << l;
+    }
+    umask[c] = m;
+    if (m) need = (unsigned)__ffsll((long long)m);
+    else unc = 1;
+  }
+  need = __reduce_max_sync(0xffffffffu, need);
+  unc = __reduce_add_sync(0xffffffffu, unc);
+  if ((threadIdx.x & 31) == 0) {
+    if (need) atomicMax(cover, (int)need);
+    if (unc) atomicAdd(cover + 1, (int)unc);
+  }
+}
+
+void collide_and_cover(const CandSet& J, const LatticeDev& lat, uint32_t* seen, const int64_t* bm_off,
+                       int64_t words, uint64_t* umask, int* cover, cudaStream_t s) {
+  const int64_t n = J.n();
+  MR1L_CUDA(cudaMemsetAsync(cover, 0, 2 * sizeof(int), s));
+  if (n == 0) return;
+  int blocks = (int)std::min<int64_t>(cdiv(n, 256), 4096);
+  collide_kernel<<<dim3(blocks, lat.L), 256, 0, s>>>(J, lat, seen, seen + words, bm_off);
+  MR1L_CHECK_LAUNCH("collide_kernel");
+  cover_kernel<<<cdiv(n, 256), 256, 0, s>>>(J, lat, seen + words, bm_off, umask, cover);
+  MR1L_CHECK_LAUNCH("cover_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 2 gather with the fused Bluestein post-chirp.
+// keys: bits(|p~|^2) + 1 for covered candidates (order-preserving for
+// non-negative doubles), 0 for uncovered ones.
+// ---------------------------------------------------------------------------
+__global__ void gather_kernel(CandSet J, LatticeDev lat, uint64_t lmask, const uint64_t* umask,
+                              const int64_t* off, const cplx* w, const cplx* C, int64_t C_stride, cplx* out,
+                              int64_t out_stride, uint64_t* keys, uint64_t* keymax) {
+  const int h = blockIdx.y;
+  const int64_t n = J.np * J.nq;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  uint64_t key = 0;
+  if (c < n) {
+    int64_t p = c / J.nq, q = c - p * J.nq;
+    uint64_t m = umask[c] & lmask;
+    int cnt = __popcll(m);
+    const cplx* Ch = C + h * C_stride;
+    cplx acc = cmake(0.0, 0.0);
+    while (m) {
+      int l = __ffsll((long long)m) - 1;
+      m &= m - 1;
+      uint32_t r = residue_of(lat, J.np, J.nq, l, p, q, (uint32_t)lat.M[l]);
+      int64_t o = off[l] + r;
+      cplx v = cmul(w[o], Ch[o]);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    cplx res = cmake(0.0, 0.0);
+    if (cnt) {
+      double inv = __drcp_rn((double)cnt);
+      res = cmake(acc.x * inv, acc.y * inv);
+      double k2 = __dadd_rn(__dmul_rn(res.x, res.x), __dmul_rn(res.y, res.y));
+      key = (uint64_t)__double_as_longlong(k2) + 1;
+    }
+    out[h * out_stride + c] = res;
+    if (keys) keys[h * n + c] = key;
+  }
+  if (keymax) {
+    key = warp_max_u64(key);
+    if ((threadIdx.x & 31) == 0 && key) atomicMax((unsigned long long*)(keymax + h), (unsigned long long)key);
+  }
+}
+
+void gather(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
+            const cplx* C, int64_t C_stride, int nrhs, cplx* p, int64_t p_stride, uint64_t* keys,
+            uint64_t* keymax, cudaStream_t s) {
+  const int64_t n = J.n();
+  if (n == 0 || nrhs == 0) return;
+  uint64_t lmask = Luse >= 64 ? ~0ull : ((1ull << Luse) - 1);
+  gather_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, g.w, C, C_stride, p,
+                                                          p_stride, keys, keymax);
+  MR1L_CHECK_LAUNCH("gather_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Scatter into lattice bins (evaluation: all lattices, weight c_k; adjoint:
+// lattices with c in I_l, weight c_k / (cnt_k M_l)).
+// ---------------------------------------------------------------------------
+__global__ void scatter_kernel(CandSet J, LatticeDev lat, uint64_t lmask, const uint64_t* umask,
+                               const int64_t* off, const cplx* coef, int64_t coef_stride, int adjoint,
+                               cplx* bins, int64_t bins_stride) {
+  const int h = blockIdx.y;
+  const int64_t n = J.np * J.nq;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  int64_t p = c / J.nq, q = c - p * J.nq;
+  cplx v = coef[h * coef_stride + c];
+  uint64_t m = lmask;
+  double inv_cnt = 1.0;
+  if (adjoint) {
+    m &= umask[c];
+    int cnt = __popcll(m);
+    if (!cnt) return;
+    inv_cnt = __drcp_rn((double)cnt);
+  }
+  cplx* B = bins + h * bins_stride;
+  while (m) {
+    int l = __ffsll((long long)m) - 1;
+    m &= m - 1;
+    uint32_t M = (uint32_t)lat.M[l];
+    uint32_t r = residue_of(lat, J.np, J.nq, l, p, q, M);
+    cplx u = v;
+    if (adjoint) {
+      double sc = inv_cnt * __drcp_rn((double)M);
+      u = cmake(v.x * sc, v.y * sc);
+    }
+    double* dst = (double*)(B + off[l] + r);
+    atomicAdd(dst, u.x);
+    atomicAdd(dst + 1, u.y);
+  }
+}
+
+void scatter(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
+             const cplx* coef, int64_t coef_stride, int nrhs, int adjoint, cplx* bins, int64_t bins_stride,
+             cudaStream_t s) {
+  const int64_t n = J.n();
+  if (n == 0 || nrhs == 0) return;
+  uint64_t lmask = Luse >= 64 ? ~0ull : ((1ull << Luse) - 1);
+  scatter_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, coef, coef_stride,
+                                                           adjoint, bins, bins_stride);
+  MR1L_CHECK_LAUNCH("scatter_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Planted sampler
+// ---------------------------------------------------------------------------
+// weight c_h exp(2 pi i sum_{j in [j0, j1) \ {skip}} h_j x_j)
+__device__ __forceinline__ cplx planted_weight(const int32_t* f, cplx c, const double* x, int j0, int j1,
+                                               int skip) {
+  double phi = 0.0;
+  for (int j = j0; j < j1; ++j)
+    if (j != skip) phi += (double)f[j] * x[j];
+  phi -= floor(phi);
+  double sn, cs;
+  sincospi(2.0 * phi, &sn, &cs);
+  return cmul(c, cmake(cs, sn));
+}
+
+__global__ void planted_lattice_kernel(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
+                                       const double* anchors, LatticeDev lat, int Luse, const int64_t* off,
+                                       cplx* bins, int64_t bins_stride) {
+  const int h = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= s_count) return;
+  const int32_t* f = freqs + i * d;
+  cplx wv = planted_weight(f, coeffs[i], anchors + (int64_t)h * d, t, d, -1);
+  cplx* B = bins + h * bins_stride;
+  for (int l = 0; l < Luse; ++l) {
+    const int64_t M = lat.M[l];
+    const int64_t* z = lat.z + (int64_t)l * lat.t;
+    int64_t acc = 0;
+    for (int j = 0; j < t; ++j) acc += (int64_t)f[j] * z[j];
+    acc %= M;
+    if (acc < 0) acc += M;
+    double* dst = (double*)(B + off[l] + acc);
+    atomicAdd(dst, wv.x);
+    atomicAdd(dst + 1, wv.y);
+  }
+}
+
+void planted_lattice_bins(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
+                          const double* anchors_dev, int nrhs, const LatticeDev& lat, int Luse,
+                          const BlueGeom& g, cplx* bins, int64_t bins_stride, cudaStream_t s) {
+  if (s_count == 0) return;
+  planted_lattice_kernel<<<dim3(cdiv(s_count, 256), nrhs), 256, 0, s>>>(freqs, coeffs, s_count, d, t, anchors_dev,
+                                                                         lat, Luse, g.off, bins, bins_stride);
+  MR1L_CHECK_LAUNCH("planted_lattice_kernel");
+}
+
+__global__ void planted_line_bins_kernel(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
+                                         int K, const double* anchors, cplx* bins) {
+  const int i = blockIdx.y;
+  const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (h >= s_count) return;
+  const int32_t* f = freqs + h * d;
+  cplx wv = planted_weight(f, coeffs[h], anchors + (int64_t)i * d, 0, d, t - 1);
+  int b = f[t - 1] % K;
+  if (b < 0) b += K;
+  double* dst = (double*)(bins + (int64_t)i * K + b);
+  atomicAdd(dst, wv.x);
+  atomicAdd(dst + 1, wv.y);
+}
+
+// y_l = sum_r B[r] exp(2 pi i l r / K) + eta_l (Philox purpose 4)
+__global__ void planted_line_eval_kernel(const cplx* bins, int K, int t, double noise_scale, uint64_t noise_seed,
+                                         int rep0, cplx* y) {
+  extern __shared__ cplx sh[];
+  cplx* ph = sh;       // exp(2 pi i m / K)
+  cplx* B = sh + K;
+  const int i = blockIdx.x;
+  for (int m = threadIdx.x; m < K; m += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)K, &sn, &cs);
+    ph[m] = cmake(cs, sn);
+    B[m] = bins[(int64_t)i * K + m];
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < K; l += blockDim.x) {
+    cplx acc = cmake(0.0, 0.0);
+    for (int r = 0; r < K; ++r) {
+      int m = (int)(((int64_t)l * r) % K);
+      cplx v = cmul(B[r], ph[m]);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    if (noise_scale != 0.0) {
+      U64Pair u = philox_u64(noise_seed, kNoiseLine, (uint32_t)t, (uint32_t)l, 0u, (uint32_t)(rep0 + i));
+      double u1 = ((double)(u.a >> 11) + 1.0) * 0x1.0p-53;
+      double u2 = (double)(u.b >> 11) * 0x1.0p-53;
+      double R = sqrt(-2.0 * log(u1));
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      acc.x += noise_scale * (R * cs);
+      acc.y += noise_scale * (R * sn);
+    }
+    y[(int64_t)i * K + l] = acc;
+  }
+}
+
+void planted_lines(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t, int K,
+                   const double* anchors_dev, int nlines, double noise_scale, uint64_t noise_seed, int rep0,
+                   cplx* bins_scratch, cplx* y, cudaStream_t s) {
+  MR1L_CUDA(cudaMemsetAsync(bins_scratch, 0, (size_t)nlines * K * sizeof(cplx), s));
+  if (s_count) {
+    planted_line_bins_kernel<<<dim3(cdiv(s_count, 256), nlines), 256, 0, s>>>(freqs, coeffs, s_count, d, t, K,
+                                                                               anchors_dev, bins_scratch);
+    MR1L_CHECK_LAUNCH("planted_line_bins_kernel");
+  }
+  size_t smem = 2 * (size_t)K * sizeof(cplx);
+  if (smem > 48 * 1024)
+    MR1L_CUDA(cudaFuncSetAttribute(planted_line_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  planted_line_eval_kernel<<<nlines, 256, smem, s>>>(bins_scratch, K, t, noise_scale, noise_seed, rep0, y);
+  MR1L_CHECK_LAUNCH("planted_line_eval_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// 1-D detection (steps 1 and 2a): one CTA per line.
+// ---------------------------------------------------------------------------
+__global__ void detect_lines_kernel(const cplx* y, int N, int64_t cap, double theta2, int rel, uint8_t* sel) {
+  extern __shared__ unsigned char shraw[];
+  const int K = 2 * N + 1;
+  cplx* ph = (cplx*)shraw;          // exp(-2 pi i m / K)
+  cplx* Y = ph + K;
+  uint64_t* key = (uint64_t*)(Y + K);
+  __shared__ uint64_t kmax;
+  const int i = blockIdx.x;
+  if (threadIdx.x == 0) kmax = 0;
+  for (int m = threadIdx.x; m < K; m += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)K, &sn, &cs);
+    ph[m] = cmake(cs, -sn);
+    Y[m] = y[(int64_t)i * K + m];
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < K; a += blockDim.x) {
+    int k = a - N;
+    int km = k < 0 ? k + K : k;
+    cplx acc = cmake(0.0, 0.0);
+    for (int l = 0; l < K; ++l) {
+      int m = (int)(((int64_t)km * l) % K);
+      cplx v = cmul(Y[l], ph[m]);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    double re = acc.x / (double)K, im = acc.y / (double)K;
+    double k2 = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+    key[a] = (uint64_t)__double_as_longlong(k2);
+    atomicMax((unsigned long long*)&kmax, (unsigned long long)key[a]);
+  }
+  __syncthreads();
+  double thr = rel ? theta2 * __longlong_as_double((long long)kmax) : theta2;
+  uint64_t tb = (uint64_t)__double_as_longlong(thr);
+  for (int a = threadIdx.x; a < K; a += blockDim.x) {
+    uint64_t ka = key[a];
+    if (ka < tb) continue;
+    int64_t rank = 0;
+    for (int b = 0; b < K; ++b) {
+      uint64_t kb = key[b];
+      rank += (kb > ka) || (kb == ka && b < a);
+    }
+    if (rank < cap) sel[a] = 1;
+  }
+}
+
+void detect_lines(const cplx* y, int nlines, int N, int64_t cap, double theta2, int rel, uint8_t* sel,
+                  cudaStream_t s) {
+  const int K = 2 * N + 1;
+  size_t smem = 2 * (size_t)K * sizeof(cplx) + (size_t)K * sizeof(uint64_t);
+  if (smem > 48 * 1024)
+    MR1L_CUDA(cudaFuncSetAttribute(detect_lines_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  detect_lines_kernel<<<nlines, 256, smem, s>>>(y, N, cap, theta2, rel, sel);
+  MR1L_CHECK_LAUNCH("detect_lines_kernel");
+}
+
+}  // namespace mr1l

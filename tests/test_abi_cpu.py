@@ -1,0 +1,75 @@
+"""The C ABI library loads and exports every entry point its header declares,
+and rejects invalid arguments on the host (no GPU needed)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1711_05152_gb300 as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(P.LIB_PATH):
+        from paper_1711_05152_gb300 import build
+        build.build()
+    return P.lib()
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:int|void)\s+(\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "mr1l_reconstruct" in names and "sfft_dimincr" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+    for n in P.EXPORTS:
+        assert n in names
+
+
+def test_version(lib):
+    assert lib.mr1l_version() >= 100
+
+
+@pytest.mark.parametrize("I,M,z,msg", [
+    ([[0], [0]], [5], [[1]], "distinct"),
+    ([[0], [1]], [6], [[1]], "prime"),
+    ([[0], [1]], [5], [[5]], "z_l"),
+    ([[0], [1]], [5, 5], [[1], [2]], "distinct"),
+    ([[40000], [1]], [5], [[1]], "2^15"),
+])
+def test_plan_rejects_invalid(lib, I, M, z, msg):
+    with pytest.raises(P.Mr1lError) as e:
+        P.plan(np.array(I), M, z, stream=0)
+    assert e.value.code == P.MR1L_E_INVAL
+    assert msg in str(e.value)
+
+
+def test_sfft_rejects_invalid(lib):
+    with pytest.raises(P.Mr1lError) as e:
+        P.sfft_dimincr(1, 4, 3, 1, 1e-12, freqs=np.zeros((1, 1)), coeffs=[1.0], stream=0)
+    assert e.value.code == P.MR1L_E_INVAL
+    with pytest.raises(P.Mr1lError) as e:
+        P.sfft_dimincr(3, 5000, 3, 1, 1e-12, freqs=np.zeros((1, 3)), coeffs=[1.0], stream=0)
+    assert e.value.code == P.MR1L_E_INVAL
+
+
+def test_null_plan_is_rejected(lib):
+    rc = lib.mr1l_reconstruct(None, None, 1, None, None)
+    assert rc == P.MR1L_E_INVAL
+    buf = ctypes.create_string_buffer(256)
+    assert lib.mr1l_last_error(buf, 256) == P.MR1L_E_INVAL
+    assert b"plan is null" in buf.value

@@ -1,0 +1,223 @@
+"""Parity of the CUDA path with the CPU oracle, element by element.
+
+Integer work (residues, collision masks, lattice choice, detected sets) must
+match bit-exactly; fp64 coefficients within 1e-10 relative error."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1711_05152_gb300 as P
+import workloads as W
+from oracle import lattice, sfft
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.lib()
+
+
+def _rand_set(rng, n, t, N):
+    J = np.unique(rng.integers(-N, N + 1, size=(int(1.5 * n) + 8, t)), axis=0)
+    rng.shuffle(J)
+    J = J[:n]
+    return J[np.lexsort(J.T[::-1])].astype(np.int64)
+
+
+def _normwise(got, want):
+    scale = max(np.max(np.abs(want)), 1e-300)
+    return np.max(np.abs(got - want)) / scale
+
+
+# sizes chosen so that P spans the one-CTA path (P <= 4096) and the 4-step
+# path, with ragged candidate counts
+SETS = [(1, 1, 3), (7, 1, 4), (50, 2, 5), (333, 3, 6), (1500, 4, 8), (9000, 5, 9), (40000, 6, 10)]
+
+
+@pytest.mark.parametrize("n,t,N", SETS)
+def test_plan_search_bitexact(n, t, N):
+    rng = np.random.default_rng(n)
+    J = _rand_set(rng, n, t, N)
+    ml = lattice.search(J, seed=n + 7, t=t)
+    pl = P.plan_search(J, seed=n + 7)
+    assert pl.L == ml.L and list(pl.M) == ml.M
+    np.testing.assert_array_equal(pl.z, np.stack(ml.z))
+    masks, res = pl.masks()
+    want_mask = np.zeros(J.shape[0], dtype=np.uint64)
+    for l, IL in enumerate(ml.unique):
+        want_mask |= IL.astype(np.uint64) << np.uint64(l)
+    np.testing.assert_array_equal(masks, want_mask)
+    for l, (M, z) in enumerate(zip(ml.M, ml.z)):
+        np.testing.assert_array_equal(res[l], lattice.residues(J, z, M))
+    assert pl.n_uncovered == int(np.sum(ml.counter() == 0))
+    assert pl.nodes == ml.nodes()
+
+
+@pytest.mark.parametrize("n,t,N", SETS)
+def test_reconstruct_parity(n, t, N):
+    rng = np.random.default_rng(100 + n)
+    J = _rand_set(rng, n, t, N)
+    pl = P.plan_search(J, seed=n)
+    ml = lattice.search(J, seed=n, t=t)
+    nrhs = 3
+    y = rng.standard_normal((nrhs, pl.sum_M)) + 1j * rng.standard_normal((nrhs, pl.sum_M))
+    got = pl.reconstruct(torch.from_numpy(y).cuda()).cpu().numpy()
+    for h in range(nrhs):
+        want, _ = lattice.reconstruct(J, ml, np.split(y[h], np.cumsum(ml.M)[:-1]), "fft")
+        assert _normwise(got[h], want) < RTOL
+
+
+@pytest.mark.parametrize("n,t,N", SETS)
+@pytest.mark.parametrize("mode", [P.MR1L_EVAL, P.MR1L_ADJOINT])
+def test_evaluate_parity(n, t, N, mode):
+    rng = np.random.default_rng(200 + n)
+    J = _rand_set(rng, n, t, N)
+    pl = P.plan_search(J, seed=n)
+    ml = lattice.search(J, seed=n, t=t)
+    c = rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))
+    got = pl.evaluate(torch.from_numpy(c).cuda(), mode).cpu().numpy()
+    for h in range(2):
+        want = np.concatenate(lattice.evaluate(J, ml, c[h], "eval" if mode == P.MR1L_EVAL else "adjoint", "fft"))
+        assert _normwise(got[h], want) < RTOL
+
+
+def test_reconstruct_direct_tier_small():
+    """Against the direct-sum oracle (no library FFT anywhere)."""
+    rng = np.random.default_rng(3)
+    J = _rand_set(rng, 120, 3, 5)
+    pl = P.plan_search(J, seed=9)
+    ml = lattice.search(J, seed=9, t=3)
+    y = rng.standard_normal(pl.sum_M) + 1j * rng.standard_normal(pl.sum_M)
+    got = pl.reconstruct(torch.from_numpy(y).cuda()).cpu().numpy()
+    want, _ = lattice.reconstruct(J, ml, np.split(y, np.cumsum(ml.M)[:-1]), "direct")
+    assert _normwise(got, want) < RTOL
+
+
+def test_given_lattice_plan_and_uncovered():
+    """mr1l_plan with explicit lattices, one frequency left uncovered: its
+    coefficient is 0; MR1L_STRICT refuses the plan."""
+    J = np.array([[0], [3], [6], [1]])
+    M, z = [3], [[1]]
+    pl = P.plan(J, M, z)
+    assert pl.n_uncovered == 3
+    y = torch.ones(3, dtype=torch.complex128, device="cuda")
+    got = pl.reconstruct(y).cpu().numpy()
+    ml = lattice.MultiLattice([3], [np.array([1])], [lattice.unique_mask(J, [1], 3)], False, 1)
+    want, _ = lattice.reconstruct(J, ml, [np.ones(3, dtype=complex)], "direct")
+    np.testing.assert_allclose(got, want, atol=1e-15)
+    with pytest.raises(P.Mr1lError) as e:
+        P.plan(J, M, z, strict=True)
+    assert e.value.code == P.MR1L_E_NOT_RECONSTRUCTING
+
+
+def test_large_single_lattice_4step():
+    """One lattice with M ~ 1.3e6 (P = 2^22, the largest 4-step split used at
+    the paper's d = 25 sizes) against numpy's FFT."""
+    M = 1_300_021
+    assert lattice.is_prime(M)
+    I = np.arange(-30000, 30000).reshape(-1, 1)
+    pl = P.plan(I, [M], [[7919]])
+    rng = np.random.default_rng(1)
+    y = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    got = pl.reconstruct(torch.from_numpy(y).cuda()).cpu().numpy()
+    ml = lattice.MultiLattice([M], [np.array([7919])], [lattice.unique_mask(I, [7919], M)], True, 1)
+    want, _ = lattice.reconstruct(I, ml, [y], "fft")
+    assert _normwise(got, want) < RTOL
+
+
+def _sfft_pair(name, seed, batch=False):
+    sig, p = W.workload(name, seed)
+    out = P.sfft_dimincr(sig.d, sig.N, p["s"], p["r"], p["theta"], p["theta_mode"], seed=seed, b=p["b"],
+                         freqs=sig.freqs, coeffs=sig.coeffs, sigma=sig.sigma, batch_reps=batch)
+    ref = sfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=seed)
+    return sig, out, ref
+
+
+def _assert_sfft_equal(out, ref):
+    for st, rs in zip(out.steps, ref.steps):
+        assert st["n_line"] == rs.I_t and st["n_cand"] == rs.n_candidates
+        assert st["L"] == rs.L and st["attempts"] == rs.attempts and st["covered"] == rs.covered
+        assert st["samples"] == rs.samples
+    np.testing.assert_array_equal(out.freqs, ref.freqs)
+    assert out.samples == ref.samples
+    rel = np.abs(out.coeffs - ref.coeffs) / np.abs(ref.coeffs)
+    assert rel.size == 0 or rel.max() < RTOL
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_sfft_tiny_d3_parity(seed):
+    sig, out, ref = _sfft_pair("tiny_d3", seed)
+    _assert_sfft_equal(out, ref)
+    np.testing.assert_array_equal(out.freqs, sig.freqs.astype(np.int64))
+
+
+def test_sfft_plain_d10_parity():
+    """The full d = 10, N = 32, s = 1000, 40 dB, r = 5 workload."""
+    sig, out, ref = _sfft_pair("plain_d10", 1)
+    assert min(s.min_gap_rank for s in ref.steps) > 1e-9, "degenerate seed (near tie)"
+    _assert_sfft_equal(out, ref)
+
+
+def test_sfft_batched_reps_identical():
+    sig, out, ref = _sfft_pair("tiny_d3", 5, batch=True)
+    _assert_sfft_equal(out, ref)
+
+
+def test_sfft_callback_sampler_matches_planted():
+    """A user sampler (here: the planted polynomial evaluated on the host and
+    copied to the device) gives the same result as the built-in one."""
+    import ctypes
+    sig, p = W.workload("tiny_d3", 6)
+    cudart = None
+    for name in ("libcudart.so", "/usr/local/cuda/lib64/libcudart.so", "libcudart.so.13"):
+        try:
+            cudart = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    if cudart is None:
+        pytest.skip("libcudart not loadable through ctypes")
+
+    def sampler(req, y_ptr, stream_ptr):
+        x = np.ctypeslib.as_array(req.anchors, shape=(req.d,)).copy()
+        if req.kind == P.SFFT_REQ_LINE:
+            vals = sfft.sample_line(sig, req.t, x, req.K, "direct")
+        else:
+            Ms = np.ctypeslib.as_array(req.M, shape=(req.L,)).tolist()
+            zs = np.ctypeslib.as_array(req.z, shape=(req.L * req.t,)).reshape(req.L, req.t)
+            ml = lattice.MultiLattice(Ms, list(zs), [], True, 1)
+            vals = np.concatenate(sfft.sample_lattice(sig, req.t, ml, x, "fft"))
+        buf = np.ascontiguousarray(vals.astype(np.complex128))
+        rc = cudart.cudaMemcpy(ctypes.c_void_p(y_ptr), buf.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.c_size_t(buf.nbytes), 1)
+        return rc
+
+    out = P.sfft_dimincr(sig.d, sig.N, p["s"], p["r"], p["theta"], p["theta_mode"], seed=6, b=p["b"],
+                         sampler=sampler)
+    ref = sfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=6)
+    _assert_sfft_equal(out, ref)
+
+
+def test_sfft_nothing_detected():
+    """Absolute threshold above every coefficient: empty output, no failure."""
+    sig, p = W.workload("tiny_d3", 7)
+    out = P.sfft_dimincr(sig.d, sig.N, p["s"], p["r"], 1e6, "abs", seed=7, freqs=sig.freqs, coeffs=sig.coeffs)
+    ref = sfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], 1e6, "abs", seed=7)
+    assert out.freqs.shape == (0, 3) and ref.freqs.shape[0] == 0
+    assert out.samples == ref.samples
+
+
+def test_sfft_d2_and_caps():
+    """d = 2 (a single lattice increment) with a cap below the support size."""
+    sig = W.planted_signal(2, 20, 60, seed=8)
+    out = P.sfft_dimincr(2, 20, 25, 2, 1e-12, "rel", seed=8, freqs=sig.freqs, coeffs=sig.coeffs)
+    ref = sfft.sfft(sig, 25, 25, 2, 10, 1e-12, "rel", seed=8)
+    _assert_sfft_equal(out, ref)
+    assert out.freqs.shape[0] == 25
