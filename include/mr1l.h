@@ -182,6 +182,7 @@ typedef struct sfft_sampler {
     int64_t s;
     double sigma;
     uint64_t noise_seed;
+    int device_arrays;      /* planted: 1 if freqs and coeffs are device pointers */
 } sfft_sampler;
 
 typedef struct sfft_params {
@@ -236,6 +237,22 @@ int sfft_dimincr(const sfft_params* params, const sfft_sampler* sampler, void* s
                  sfft_result** out);
 
 void sfft_free(sfft_result* res);
+
+/* ------------------------------------------------------------------------ */
+/* Launch accounting and kernel timing                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Every kernel launch of the library is counted.  With profiling enabled,
+ * each launch is also bracketed by CUDA events on its own stream together
+ * with its algorithmic flops and bytes (FFT flops by the 5 n log2 n
+ * convention).  mr1l_prof_read writes a JSON object
+ *   {"kernel": {"launches": n, "ms": total, "flops": f, "bytes": b}, ...}
+ * into buf (len bytes), synchronising the recorded events; it fails with
+ * MR1L_E_INVAL when buf is too small. */
+int mr1l_prof_enable(int on);
+int mr1l_prof_reset(void);
+long long mr1l_prof_launches(void);
+int mr1l_prof_read(char* buf, size_t len);
 
 #ifdef __cplusplus
 }

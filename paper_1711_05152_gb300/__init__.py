@@ -41,7 +41,7 @@ SFFT_MAX_STEPS = 256
 EXPORTS = [
     "mr1l_last_error", "mr1l_version", "mr1l_plan", "mr1l_plan_search", "mr1l_plan_info",
     "mr1l_plan_masks", "mr1l_destroy", "mr1l_reconstruct", "mr1l_evaluate", "sfft_dimincr",
-    "sfft_free",
+    "sfft_free", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
 ]
 
 
@@ -63,7 +63,7 @@ SAMPLE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(sfft_request), C.c_void_p
 class sfft_sampler(C.Structure):
     _fields_ = [("fn", SAMPLE_FN), ("user", C.c_void_p), ("freqs", C.POINTER(C.c_int32)),
                 ("coeffs", C.POINTER(C.c_double)), ("s", C.c_int64), ("sigma", C.c_double),
-                ("noise_seed", C.c_uint64)]
+                ("noise_seed", C.c_uint64), ("device_arrays", C.c_int)]
 
 
 class sfft_params(C.Structure):
@@ -115,6 +115,11 @@ def lib() -> C.CDLL:
                                C.POINTER(C.POINTER(sfft_result))]
     L.sfft_free.argtypes = [C.POINTER(sfft_result)]
     L.sfft_free.restype = None
+    L.mr1l_prof_enable.argtypes = [C.c_int]
+    L.mr1l_prof_reset.argtypes = []
+    L.mr1l_prof_launches.argtypes = []
+    L.mr1l_prof_launches.restype = C.c_longlong
+    L.mr1l_prof_read.argtypes = [C.c_char_p, C.c_size_t]
     _lib = L
     return L
 

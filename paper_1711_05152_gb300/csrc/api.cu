@@ -243,6 +243,7 @@ struct LatticeWork {
     geom.Bh = Bh.get();
     geom.tw = twiddle_table(logP, s);
     geom.twn = small_twiddles(s);
+    geom.sum_M = sumM;
     chirp_tables(geom, maxM, s);
     blue_filter(geom, s);
   }
@@ -481,9 +482,11 @@ struct SfftRun {
   double theta2;
   int rel;
   sfft_stats stats{};
-  // planted signal on the device
-  DevBuf<int32_t> freqs;
-  DevBuf<cplx> coeffs;
+  // planted signal on the device (copied, or the caller's device arrays)
+  DevBuf<int32_t> freqs_buf;
+  DevBuf<cplx> coeffs_buf;
+  const int32_t* freqs_ptr = nullptr;
+  const cplx* coeffs_ptr = nullptr;
   // candidate prefix (device + host mirror) and last list
   DevBuf<int32_t> pre, pre_next, last;
   std::vector<int32_t> pre_h;
@@ -543,7 +546,7 @@ struct SfftRun {
         if (rc != 0) throw Error(MR1L_E_SAMPLER, "sampler callback failed (line request)");
       }
     } else {
-      planted_lines(freqs.get(), coeffs.get(), S.s, P.d, t, K, anchors.get(), r, S.sigma / std::sqrt(2.0),
+      planted_lines(freqs_ptr, coeffs_ptr, S.s, P.d, t, K, anchors.get(), r, S.sigma / std::sqrt(2.0),
                     S.noise_seed, 0, line_bins.get(), line_y.get(), s);
     }
     ev_record();
@@ -588,7 +591,7 @@ struct SfftRun {
     } else {
       bins.reserve((size_t)nrep * sumM);
       MR1L_CUDA(cudaMemsetAsync(bins.get(), 0, (size_t)nrep * sumM * sizeof(cplx), s));
-      planted_lattice_bins(freqs.get(), coeffs.get(), S.s, P.d, t, anchors.get(), nrep, lw.dev(), lw.Luse, lw.geom,
+      planted_lattice_bins(freqs_ptr, coeffs_ptr, S.s, P.d, t, anchors.get(), nrep, lw.dev(), lw.Luse, lw.geom,
                            bins.get(), sumM, s);
       BlueIO io{};
       io.in = bins.get();
@@ -628,13 +631,18 @@ struct SfftRun {
     K = 2 * P.N + 1;
     theta2 = P.theta * P.theta;
     rel = P.theta_mode == SFFT_THETA_REL;
-    if (!S.fn) {
-      freqs.reserve(std::max<int64_t>(S.s * d, 1));
-      coeffs.reserve(std::max<int64_t>(S.s, 1));
+    if (!S.fn && !S.device_arrays) {
+      freqs_buf.reserve(std::max<int64_t>(S.s * d, 1));
+      coeffs_buf.reserve(std::max<int64_t>(S.s, 1));
       if (S.s) {
-        MR1L_CUDA(cudaMemcpyAsync(freqs.get(), S.freqs, S.s * d * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        MR1L_CUDA(cudaMemcpyAsync(coeffs.get(), S.coeffs, S.s * sizeof(cplx), cudaMemcpyHostToDevice, s));
+        MR1L_CUDA(cudaMemcpyAsync(freqs_buf.get(), S.freqs, S.s * d * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        MR1L_CUDA(cudaMemcpyAsync(coeffs_buf.get(), S.coeffs, S.s * sizeof(cplx), cudaMemcpyHostToDevice, s));
       }
+      freqs_ptr = freqs_buf.get();
+      coeffs_ptr = (const cplx*)coeffs_buf.get();
+    } else if (!S.fn) {
+      freqs_ptr = S.freqs;
+      coeffs_ptr = (const cplx*)S.coeffs;
     }
     // step 1
     std::vector<int32_t> I1 = detect(1);
@@ -763,8 +771,9 @@ extern "C" int sfft_dimincr(const sfft_params* params, const sfft_sampler* sampl
       MR1L_REQUIRE(sampler->s >= 0, "planted s must be >= 0");
       MR1L_REQUIRE(sampler->s == 0 || (sampler->freqs && sampler->coeffs), "planted arrays are null");
       MR1L_REQUIRE(sampler->sigma >= 0.0, "sigma must be >= 0");
-      for (int64_t i = 0; i < sampler->s * P.d; ++i)
-        MR1L_REQUIRE(sampler->freqs[i] > -32768 && sampler->freqs[i] < 32768, "|h_j| must be < 2^15");
+      if (!sampler->device_arrays)
+        for (int64_t i = 0; i < sampler->s * P.d; ++i)
+          MR1L_REQUIRE(sampler->freqs[i] > -32768 && sampler->freqs[i] < 32768, "|h_j| must be < 2^15");
     }
     std::unique_ptr<SfftRun> run(new SfftRun());
     run->P = P;

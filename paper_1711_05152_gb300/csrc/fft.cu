@@ -23,7 +23,10 @@
 #include <map>
 #include <mutex>
 
+#include <cmath>
+
 #include "fft.cuh"
+#include "prof.cuh"
 
 namespace mr1l {
 
@@ -367,8 +370,7 @@ const cplx* twiddle_table(int logP, cudaStream_t s) {
   int64_t P = int64_t(1) << logP;
   cplx* p = nullptr;
   MR1L_CUDA(cudaMalloc(&p, P * sizeof(cplx)));
-  twiddle_kernel<<<cdiv(P, 256), 256, 0, s>>>(p, P);
-  MR1L_CHECK_LAUNCH("twiddle_kernel");
+  MR1L_LAUNCH("twiddle_kernel", s, 0, 16.0 * P, twiddle_kernel<<<cdiv(P, 256), 256, 0, s>>>(p, P));
   MR1L_CUDA(cudaStreamSynchronize(s));
   g_tw[key] = p;
   return p;
@@ -383,8 +385,7 @@ const cplx* small_twiddles(cudaStream_t s) {
   cplx* p = nullptr;
   MR1L_CUDA(cudaMalloc(&p, 8192 * sizeof(cplx)));
   MR1L_CUDA(cudaMemsetAsync(p, 0, 8192 * sizeof(cplx), s));
-  small_twiddle_kernel<<<32, 256, 0, s>>>(p);
-  MR1L_CHECK_LAUNCH("small_twiddle_kernel");
+  MR1L_LAUNCH("small_twiddle_kernel", s, 0, 16.0 * 8192, small_twiddle_kernel<<<32, 256, 0, s>>>(p));
   MR1L_CUDA(cudaStreamSynchronize(s));
   g_twn[dev] = p;
   return p;
@@ -406,8 +407,8 @@ void blue_split(BlueGeom& g, int logP) {
 
 void chirp_tables(const BlueGeom& g, int64_t max_M, cudaStream_t s) {
   dim3 grid(cdiv(max_M, 256), g.L);
-  chirp_kernel<<<grid, 256, 0, s>>>(const_cast<cplx*>(g.w), const_cast<cplx*>(g.ws), g.off, g.M, g.L);
-  MR1L_CHECK_LAUNCH("chirp_kernel");
+  MR1L_LAUNCH("chirp_kernel", s, 0, 32.0 * g.sum_M,
+              chirp_kernel<<<grid, 256, 0, s>>>(const_cast<cplx*>(g.w), const_cast<cplx*>(g.ws), g.off, g.M, g.L));
 }
 
 template <typename K>
@@ -421,34 +422,47 @@ static int threads_for(int elems) {
   return t;
 }
 
+static double fft_flops(double n) { return n > 1 ? 5.0 * n * std::log2(n) : 0.0; }
+
+// Algorithmic work of one launch (FFT flops by the 5 n log2 n convention plus
+// 6 flops per complex multiply; bytes that the pass must move).
 template <int MODE>
 static void launch_first_last(const BlueGeom& g, const BlueIO& io, int ntrans, cudaStream_t s) {
+  const double P = g.P, nr = (double)ntrans / g.L, sumM = (double)g.sum_M;
+  const double cb = sizeof(cplx);
   if (g.logP <= kSmallLog) {
     size_t smem = (size_t)g.P * sizeof(cplx);
     set_smem(blue_small_kernel<MODE>, smem);
-    blue_small_kernel<MODE><<<ntrans, threads_for(g.P), smem, s>>>(g, io);
-    MR1L_CHECK_LAUNCH("blue_small_kernel");
+    double fl = ntrans * (MODE == kModeFilter ? fft_flops(P) : 2 * fft_flops(P) + 6 * P) + nr * 6 * sumM;
+    double by = MODE == kModeFilter ? g.L * P * cb + sumM * cb : nr * sumM * cb * 3 + ntrans * P * cb;
+    MR1L_LAUNCH(MODE == kModeFilter ? "blue_small_filter" : (MODE == kModeRecon ? "blue_small_recon" : "blue_small_eval"),
+                s, fl, by, blue_small_kernel<MODE><<<ntrans, threads_for(g.P), smem, s>>>(g, io));
     return;
   }
   int CB = col_tile(g.P1), RB = row_tile(g.P2);
   size_t smem_c = (size_t)g.P1 * CB * sizeof(cplx);
   size_t smem_r = (size_t)RB * g.P2 * sizeof(cplx);
   dim3 gc(g.P2 / CB, ntrans), gr(g.P1 / RB, ntrans);
+  const double P1 = g.P1, P2 = g.P2;
   set_smem(blue_col_fwd_kernel<MODE>, smem_c);
-  blue_col_fwd_kernel<MODE><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io);
-  MR1L_CHECK_LAUNCH("blue_col_fwd_kernel");
+  MR1L_LAUNCH(MODE == kModeFilter ? "blue_col_fwd_filter" : (MODE == kModeRecon ? "blue_col_fwd_recon" : "blue_col_fwd_eval"),
+              s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM, nr * sumM * cb * 2 + ntrans * P * cb,
+              blue_col_fwd_kernel<MODE><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
   if (MODE == kModeFilter) {
     set_smem(blue_row_kernel<true>, smem_r);
-    blue_row_kernel<true><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io);
-    MR1L_CHECK_LAUNCH("blue_row_kernel<filter>");
+    MR1L_LAUNCH("blue_row_filter", s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
+                blue_row_kernel<true><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
     return;
   }
   set_smem(blue_row_kernel<false>, smem_r);
-  blue_row_kernel<false><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io);
-  MR1L_CHECK_LAUNCH("blue_row_kernel");
+  MR1L_LAUNCH(MODE == kModeRecon ? "blue_row_recon" : "blue_row_eval", s,
+              ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
+              blue_row_kernel<false><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
   set_smem(blue_col_inv_kernel<MODE>, smem_c);
-  blue_col_inv_kernel<MODE><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io);
-  MR1L_CHECK_LAUNCH("blue_col_inv_kernel");
+  MR1L_LAUNCH(MODE == kModeRecon ? "blue_col_inv_recon" : "blue_col_inv_eval", s,
+              ntrans * P2 * fft_flops(P1) + (MODE == kModeEval ? nr * 6 * sumM : 0.0),
+              ntrans * P * cb + nr * sumM * cb * (MODE == kModeEval ? 2 : 1),
+              blue_col_inv_kernel<MODE><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
 }
 
 void blue_filter(const BlueGeom& g, cudaStream_t s) {

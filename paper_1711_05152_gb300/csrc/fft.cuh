@@ -25,6 +25,7 @@ struct BlueGeom {
   cplx* Bh;             // device [L][P]: filter spectrum FFT_P(b) / P (pass order)
   const cplx* tw;       // device [P]: exp(-2 pi i e / P)
   const cplx* twn;      // device [8192]: exp(-2 pi i e / n) for n = 2..4096 at offset n
+  int64_t sum_M;        // host: sum of the L lattice sizes (for launch accounting)
 };
 
 struct BlueIO {

@@ -2,6 +2,7 @@
 // averaged gather of Algorithm 2, scatter into lattice bins, the planted
 // sampler and the 1-D line detection of Algorithm 3.
 #include "ops.cuh"
+#include "prof.cuh"
 
 namespace mr1l {
 
@@ -52,11 +53,9 @@ __global__ void last_res_kernel(CandSet J, LatticeDev lat) {
 
 void residues(const CandSet& J, const LatticeDev& lat, cudaStream_t s) {
   if (J.np > 0) {
-    pre_res_kernel<<<dim3(cdiv(J.np, 256), lat.L), 256, 0, s>>>(J, lat);
-    MR1L_CHECK_LAUNCH("pre_res_kernel");
+    MR1L_LAUNCH("pre_res_kernel", s, 0, 0, pre_res_kernel<<<dim3(cdiv(J.np, 256), lat.L), 256, 0, s>>>(J, lat));
   }
-  last_res_kernel<<<dim3(cdiv(J.nq, 256), lat.L), 256, 0, s>>>(J, lat);
-  MR1L_CHECK_LAUNCH("last_res_kernel");
+  MR1L_LAUNCH("last_res_kernel", s, 0, 0, last_res_kernel<<<dim3(cdiv(J.nq, 256), lat.L), 256, 0, s>>>(J, lat));
 }
 
 // ---------------------------------------------------------------------------
@@ -111,10 +110,8 @@ void collide_and_cover(const CandSet& J, const LatticeDev& lat, uint32_t* seen, 
   MR1L_CUDA(cudaMemsetAsync(cover, 0, 2 * sizeof(int), s));
   if (n == 0) return;
   int blocks = (int)std::min<int64_t>(cdiv(n, 256), 4096);
-  collide_kernel<<<dim3(blocks, lat.L), 256, 0, s>>>(J, lat, seen, seen + words, bm_off);
-  MR1L_CHECK_LAUNCH("collide_kernel");
-  cover_kernel<<<cdiv(n, 256), 256, 0, s>>>(J, lat, seen + words, bm_off, umask, cover);
-  MR1L_CHECK_LAUNCH("cover_kernel");
+  MR1L_LAUNCH("collide_kernel", s, 0, 0, collide_kernel<<<dim3(blocks, lat.L), 256, 0, s>>>(J, lat, seen, seen + words, bm_off));
+  MR1L_LAUNCH("cover_kernel", s, 0, 0, cover_kernel<<<cdiv(n, 256), 256, 0, s>>>(J, lat, seen + words, bm_off, umask, cover));
 }
 
 // ---------------------------------------------------------------------------
@@ -166,9 +163,8 @@ void gather(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* u
   const int64_t n = J.n();
   if (n == 0 || nrhs == 0) return;
   uint64_t lmask = Luse >= 64 ? ~0ull : ((1ull << Luse) - 1);
-  gather_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, g.w, C, C_stride, p,
-                                                          p_stride, keys, keymax);
-  MR1L_CHECK_LAUNCH("gather_kernel");
+  MR1L_LAUNCH("gather_kernel", s, 0, 0, gather_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, g.w, C, C_stride, p,
+                                                          p_stride, keys, keymax));
 }
 
 // ---------------------------------------------------------------------------
@@ -215,9 +211,8 @@ void scatter(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* 
   const int64_t n = J.n();
   if (n == 0 || nrhs == 0) return;
   uint64_t lmask = Luse >= 64 ? ~0ull : ((1ull << Luse) - 1);
-  scatter_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, coef, coef_stride,
-                                                           adjoint, bins, bins_stride);
-  MR1L_CHECK_LAUNCH("scatter_kernel");
+  MR1L_LAUNCH("scatter_kernel", s, 0, 0, scatter_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, coef, coef_stride,
+                                                           adjoint, bins, bins_stride));
 }
 
 // ---------------------------------------------------------------------------
@@ -261,9 +256,8 @@ void planted_lattice_bins(const int32_t* freqs, const cplx* coeffs, int64_t s_co
                           const double* anchors_dev, int nrhs, const LatticeDev& lat, int Luse,
                           const BlueGeom& g, cplx* bins, int64_t bins_stride, cudaStream_t s) {
   if (s_count == 0) return;
-  planted_lattice_kernel<<<dim3(cdiv(s_count, 256), nrhs), 256, 0, s>>>(freqs, coeffs, s_count, d, t, anchors_dev,
-                                                                         lat, Luse, g.off, bins, bins_stride);
-  MR1L_CHECK_LAUNCH("planted_lattice_kernel");
+  MR1L_LAUNCH("planted_lattice_kernel", s, 0, 0, planted_lattice_kernel<<<dim3(cdiv(s_count, 256), nrhs), 256, 0, s>>>(freqs, coeffs, s_count, d, t, anchors_dev,
+                                                                         lat, Luse, g.off, bins, bins_stride));
 }
 
 __global__ void planted_line_bins_kernel(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
@@ -321,15 +315,13 @@ void planted_lines(const int32_t* freqs, const cplx* coeffs, int64_t s_count, in
                    cplx* bins_scratch, cplx* y, cudaStream_t s) {
   MR1L_CUDA(cudaMemsetAsync(bins_scratch, 0, (size_t)nlines * K * sizeof(cplx), s));
   if (s_count) {
-    planted_line_bins_kernel<<<dim3(cdiv(s_count, 256), nlines), 256, 0, s>>>(freqs, coeffs, s_count, d, t, K,
-                                                                               anchors_dev, bins_scratch);
-    MR1L_CHECK_LAUNCH("planted_line_bins_kernel");
+    MR1L_LAUNCH("planted_line_bins_kernel", s, 0, 0, planted_line_bins_kernel<<<dim3(cdiv(s_count, 256), nlines), 256, 0, s>>>(freqs, coeffs, s_count, d, t, K,
+                                                                               anchors_dev, bins_scratch));
   }
   size_t smem = 2 * (size_t)K * sizeof(cplx);
   if (smem > 48 * 1024)
     MR1L_CUDA(cudaFuncSetAttribute(planted_line_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  planted_line_eval_kernel<<<nlines, 256, smem, s>>>(bins_scratch, K, t, noise_scale, noise_seed, rep0, y);
-  MR1L_CHECK_LAUNCH("planted_line_eval_kernel");
+  MR1L_LAUNCH("planted_line_eval_kernel", s, 0, 0, planted_line_eval_kernel<<<nlines, 256, smem, s>>>(bins_scratch, K, t, noise_scale, noise_seed, rep0, y));
 }
 
 // ---------------------------------------------------------------------------
@@ -387,8 +379,7 @@ void detect_lines(const cplx* y, int nlines, int N, int64_t cap, double theta2, 
   size_t smem = 2 * (size_t)K * sizeof(cplx) + (size_t)K * sizeof(uint64_t);
   if (smem > 48 * 1024)
     MR1L_CUDA(cudaFuncSetAttribute(detect_lines_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  detect_lines_kernel<<<nlines, 256, smem, s>>>(y, N, cap, theta2, rel, sel);
-  MR1L_CHECK_LAUNCH("detect_lines_kernel");
+  MR1L_LAUNCH("detect_lines_kernel", s, 0, 0, detect_lines_kernel<<<nlines, 256, smem, s>>>(y, N, cap, theta2, rel, sel));
 }
 
 }  // namespace mr1l

@@ -8,6 +8,7 @@
 // pick, then a marking pass.  Ties at the cut are broken by the smaller
 // candidate id, as the (lexicographic) candidate order demands.
 #include "ops.cuh"
+#include "prof.cuh"
 
 namespace mr1l {
 
@@ -127,19 +128,14 @@ __global__ void sel_tie_kernel(const uint64_t* keys, int64_t n, const SelectStat
 void select_topk(const uint64_t* keys, int64_t n, int nrhs, const uint64_t* keymax, double theta2, int rel,
                  int64_t cap, SelectState* st, uint8_t* flags, cudaStream_t s) {
   if (n == 0 || nrhs == 0) return;
-  sel_init_kernel<<<cdiv(nrhs, 64), 64, 0, s>>>(st, keymax, theta2, rel, nrhs);
-  MR1L_CHECK_LAUNCH("sel_init_kernel");
+  MR1L_LAUNCH("sel_init_kernel", s, 0, 0, sel_init_kernel<<<cdiv(nrhs, 64), 64, 0, s>>>(st, keymax, theta2, rel, nrhs));
   int blocks = (int)std::min<int64_t>(cdiv(n, 1024), 304);
   for (int pass = 0; pass < 8; ++pass) {
-    sel_hist_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, pass);
-    MR1L_CHECK_LAUNCH("sel_hist_kernel");
-    sel_pick_kernel<<<nrhs, 32, 0, s>>>(st, cap, pass);
-    MR1L_CHECK_LAUNCH("sel_pick_kernel");
+    MR1L_LAUNCH("sel_hist_kernel", s, 0, 0, sel_hist_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, pass));
+    MR1L_LAUNCH("sel_pick_kernel", s, 0, 0, sel_pick_kernel<<<nrhs, 32, 0, s>>>(st, cap, pass));
   }
-  sel_mark_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, flags);
-  MR1L_CHECK_LAUNCH("sel_mark_kernel");
-  sel_tie_kernel<<<nrhs, 1024, 0, s>>>(keys, n, st, flags);
-  MR1L_CHECK_LAUNCH("sel_tie_kernel");
+  MR1L_LAUNCH("sel_mark_kernel", s, 0, 0, sel_mark_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, flags));
+  MR1L_LAUNCH("sel_tie_kernel", s, 0, 0, sel_tie_kernel<<<nrhs, 1024, 0, s>>>(keys, n, st, flags));
 }
 
 // ---------------------------------------------------------------------------
@@ -205,13 +201,10 @@ int64_t compact(const CandSet& J, const uint8_t* flags, int32_t* out_rows, const
   if (n == 0) return 0;
   const int64_t nblocks = cdiv(n, kCompactBlock);
   MR1L_REQUIRE(scratch_len >= nblocks + 1, "compaction scratch too small");
-  compact_count_kernel<<<nblocks, kCompactBlock, 0, s>>>(flags, n, scratch_counts);
-  MR1L_CHECK_LAUNCH("compact_count_kernel");
-  compact_scan_kernel<<<1, kCompactBlock, 0, s>>>(scratch_counts, nblocks);
-  MR1L_CHECK_LAUNCH("compact_scan_kernel");
+  MR1L_LAUNCH("compact_count_kernel", s, 0, 0, compact_count_kernel<<<nblocks, kCompactBlock, 0, s>>>(flags, n, scratch_counts));
+  MR1L_LAUNCH("compact_scan_kernel", s, 0, 0, compact_scan_kernel<<<1, kCompactBlock, 0, s>>>(scratch_counts, nblocks));
   if (out_rows || out_p) {
-    compact_scatter_kernel<<<nblocks, kCompactBlock, 0, s>>>(J, flags, scratch_counts, out_rows, p, out_p);
-    MR1L_CHECK_LAUNCH("compact_scatter_kernel");
+    MR1L_LAUNCH("compact_scatter_kernel", s, 0, 0, compact_scatter_kernel<<<nblocks, kCompactBlock, 0, s>>>(J, flags, scratch_counts, out_rows, p, out_p));
   }
   int64_t total = 0;
   MR1L_CUDA(cudaMemcpyAsync(&total, scratch_counts + nblocks, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

@@ -27,7 +27,7 @@ def _declared():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"^\s*(?:int|void)\s+(\w+)\s*\(", src, flags=re.M)
+            names += re.findall(r"^\s*(?:int|void|long long)\s+(\w+)\s*\(", src, flags=re.M)
     return names
 
 
