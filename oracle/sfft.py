@@ -205,7 +205,10 @@ def candidates(prefix: np.ndarray, last: np.ndarray) -> np.ndarray:
 
 
 def sfft(sig, s: int, s_local: int, r: int, b: int, theta: float, theta_mode: str,
-         seed: int, dft: str = "fft") -> SfftResult:
+         seed: int, dft: str = "fft", t_stop: int | None = None) -> SfftResult:
+    """Algorithm 3.  t_stop (optional) ends the run after that dimension
+    increment (a bounded sample of the work; the result is then the
+    projected set I^(1..t_stop))."""
     d = sig.d
     if d < 2:
         raise ValueError("the dimension-incremental method needs d >= 2")
@@ -218,6 +221,8 @@ def sfft(sig, s: int, s_local: int, r: int, b: int, theta: float, theta_mode: st
     prefix = I1.reshape(-1, 1)
     coeffs = np.zeros(0, dtype=np.complex128)
     for t in range(2, d + 1):
+        if t_stop is not None and t > t_stop:
+            break
         It, gr, gt = detect_1d(sig, t, seed, r, s_local, theta, theta_mode, dft)
         lines.append(It)
         rt, st = (r, s_local) if t < d else (1, s)

@@ -276,12 +276,23 @@ def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str =
                     theta_mode=SFFT_THETA_REL if theta_mode == "rel" else SFFT_THETA_ABS, seed=seed,
                     batch_reps=1 if batch_reps else 0)
     keep = []
-    if sampler is None:
+    nseed = seed if noise_seed is None else noise_seed
+    if sampler is None and getattr(freqs, "is_cuda", False):
+        # planted signal already resident on the device (int32 [s, d], complex128 [s])
+        import torch
+        if freqs.dtype != torch.int32 or coeffs.dtype != torch.complex128 or not (
+                freqs.is_contiguous() and coeffs.is_contiguous()):
+            raise TypeError("device planted arrays must be contiguous int32 / complex128")
+        keep += [freqs, coeffs]
+        samp = sfft_sampler(SAMPLE_FN(), None, C.cast(C.c_void_p(freqs.data_ptr()), C.POINTER(C.c_int32)),
+                            C.cast(C.c_void_p(coeffs.data_ptr()), C.POINTER(C.c_double)), freqs.shape[0], sigma,
+                            nseed, 1)
+    elif sampler is None:
         f = _i32(freqs).reshape(-1, d)
         c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.complex128)).view(np.float64)
         keep += [f, c]
         samp = sfft_sampler(SAMPLE_FN(), None, _ptr(f, C.c_int32), _ptr(c, C.c_double), f.shape[0], sigma,
-                            seed if noise_seed is None else noise_seed)
+                            nseed, 0)
     else:
         def _cb(user, req, y, stream_ptr):
             try:
@@ -292,7 +303,7 @@ def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str =
                 return 1
         fn = SAMPLE_FN(_cb)
         keep.append(fn)
-        samp = sfft_sampler(fn, None, None, None, 0, 0.0, 0)
+        samp = sfft_sampler(fn, None, None, None, 0, 0.0, 0, 0)
     out = C.POINTER(sfft_result)()
     _check(lib().sfft_dimincr(C.byref(p), C.byref(samp), C.c_void_p(_stream(stream)), C.byref(out)))
     try:
@@ -310,3 +321,25 @@ def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str =
         return SfftOutput(fr, cf, st.samples, st.ms_total, st.ms_sampling, steps)
     finally:
         lib().sfft_free(out)
+
+
+def prof_enable(on: bool = True) -> None:
+    """Bracket every library kernel launch with CUDA events (see mr1l_prof_read)."""
+    _check(lib().mr1l_prof_enable(1 if on else 0))
+
+
+def prof_reset() -> None:
+    _check(lib().mr1l_prof_reset())
+
+
+def prof_launches() -> int:
+    """Kernel launches of the library since the last reset."""
+    return int(lib().mr1l_prof_launches())
+
+
+def prof_read() -> dict:
+    """Per-kernel totals {name: {launches, ms, flops, bytes}} since the last reset."""
+    import json
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().mr1l_prof_read(buf, 1 << 16))
+    return json.loads(buf.value.decode())
