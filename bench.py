@@ -356,6 +356,27 @@ def run_ours(args):
     return 0
 
 
+def run_kernel_case(args):
+    """The lattice transform alone at the bench workload's size (|J| = 65 x
+    1000 candidates in Z^10, Algorithm 1 lattice, 5 right-hand sides): one
+    warm-up and one measured reconstruct + adjoint, for ncu captures."""
+    import torch
+
+    import paper_1711_05152_gb300 as P
+    rng = np.random.default_rng(args.seed)
+    pre = np.unique(rng.integers(-32, 33, size=(1100, 9)), axis=0)[:1000]
+    J = np.concatenate([np.repeat(pre, 65, axis=0), np.tile(np.arange(-32, 33), 1000)[:, None]], axis=1)
+    pl = P.plan_search(J, seed=args.seed)
+    y = torch.from_numpy(W.complex_normal(rng, (5, pl.sum_M))).cuda()
+    for _ in range(2):
+        c = pl.reconstruct(y)
+        pl.evaluate(c, P.MR1L_ADJOINT)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": "reconstruct+adjoint", "n": int(J.shape[0]), "L": pl.L,
+                      "sum_M": int(pl.sum_M), "M0": int(pl.M[0])}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,7 +385,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="run only the lattice transform at the workload size (for ncu captures)")
     args = ap.parse_args()
+    if args.kernel_case:
+        return run_kernel_case(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

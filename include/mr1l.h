@@ -238,6 +238,19 @@ int sfft_dimincr(const sfft_params* params, const sfft_sampler* sampler, void* s
 
 void sfft_free(sfft_result* res);
 
+/*
+ * sfft_dimincr_batch - Algorithm 3 on `count` independent problems
+ * (params[i], samplers[i]; uneven d, N, s allowed).  Up to `concurrency`
+ * problems run at once, each on its own non-blocking CUDA stream driven by its
+ * own host worker, so the small launches of one problem overlap the work of
+ * the others.  out[i] receives problem i's result (free each with sfft_free)
+ * and status[i] its status; the call returns the first failure's status (the
+ * other problems still run).  Host arrays of every sampler must stay valid
+ * for the whole call.
+ */
+int sfft_dimincr_batch(const sfft_params* params, const sfft_sampler* samplers, int count, int concurrency,
+                       sfft_result** out, int* status);
+
 /* ------------------------------------------------------------------------ */
 /* Launch accounting and kernel timing                                       */
 /* ------------------------------------------------------------------------ */

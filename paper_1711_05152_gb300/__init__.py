@@ -41,7 +41,7 @@ SFFT_MAX_STEPS = 256
 EXPORTS = [
     "mr1l_last_error", "mr1l_version", "mr1l_plan", "mr1l_plan_search", "mr1l_plan_info",
     "mr1l_plan_masks", "mr1l_destroy", "mr1l_reconstruct", "mr1l_evaluate", "sfft_dimincr",
-    "sfft_free", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
+    "sfft_free", "sfft_dimincr_batch", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
 ]
 
 
@@ -115,6 +115,8 @@ def lib() -> C.CDLL:
                                C.POINTER(C.POINTER(sfft_result))]
     L.sfft_free.argtypes = [C.POINTER(sfft_result)]
     L.sfft_free.restype = None
+    L.sfft_dimincr_batch.argtypes = [C.POINTER(sfft_params), C.POINTER(sfft_sampler), C.c_int, C.c_int,
+                                     C.POINTER(C.POINTER(sfft_result)), C.POINTER(C.c_int)]
     L.mr1l_prof_enable.argtypes = [C.c_int]
     L.mr1l_prof_reset.argtypes = []
     L.mr1l_prof_launches.argtypes = []
@@ -307,21 +309,53 @@ def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str =
     out = C.POINTER(sfft_result)()
     _check(lib().sfft_dimincr(C.byref(p), C.byref(samp), C.c_void_p(_stream(stream)), C.byref(out)))
     try:
-        res = out.contents
-        n = res.n
-        fr = np.ctypeslib.as_array(res.freqs, shape=(max(n, 1) * d,))[: n * d].astype(np.int64).reshape(n, d)
-        cf = np.ctypeslib.as_array(res.coeffs, shape=(max(n, 1) * 2,))[: 2 * n].copy().view(np.complex128)
-        st = res.stats
-        steps = []
-        for i in range(st.n_steps):
-            x = st.steps[i]
-            steps.append(dict(t=x.t, n_line=x.n_line, n_cand=x.n_cand, L=x.L, attempts=x.attempts,
-                              covered=bool(x.covered), sum_M=x.sum_M, samples=x.samples,
-                              n_detected=x.n_detected))
-        return SfftOutput(fr, cf, st.samples, st.ms_total, st.ms_sampling, steps)
+        return _convert(out.contents, d)
     finally:
         lib().sfft_free(out)
 
+
+def _convert(res: sfft_result, d: int) -> SfftOutput:
+    n = res.n
+    fr = np.ctypeslib.as_array(res.freqs, shape=(max(n, 1) * d,))[: n * d].astype(np.int64).reshape(n, d)
+    cf = np.ctypeslib.as_array(res.coeffs, shape=(max(n, 1) * 2,))[: 2 * n].copy().view(np.complex128)
+    st = res.stats
+    steps = []
+    for i in range(st.n_steps):
+        x = st.steps[i]
+        steps.append(dict(t=x.t, n_line=x.n_line, n_cand=x.n_cand, L=x.L, attempts=x.attempts,
+                          covered=bool(x.covered), sum_M=x.sum_M, samples=x.samples, n_detected=x.n_detected))
+    return SfftOutput(fr, cf, st.samples, st.ms_total, st.ms_sampling, steps)
+
+
+def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[SfftOutput]:
+    """Algorithm 3 on many independent planted problems at once.  Each problem
+    is a dict with d, N, s, r, theta, theta_mode, seed, freqs, coeffs and
+    optionally sigma, s_local, b, noise_seed, batch_reps."""
+    n = len(problems)
+    params = (sfft_params * max(n, 1))()
+    samps = (sfft_sampler * max(n, 1))()
+    keep = []
+    for i, q in enumerate(problems):
+        d = q["d"]
+        params[i] = sfft_params(d=d, N=q["N"], s=q["s"], s_local=q.get("s_local", q["s"]), r=q["r"],
+                                b=q.get("b", 10), theta=q["theta"],
+                                theta_mode=SFFT_THETA_REL if q.get("theta_mode", "rel") == "rel" else SFFT_THETA_ABS,
+                                seed=q["seed"], batch_reps=1 if q.get("batch_reps", True) else 0)
+        f = _i32(q["freqs"]).reshape(-1, d)
+        c = np.ascontiguousarray(np.asarray(q["coeffs"], dtype=np.complex128)).view(np.float64)
+        keep += [f, c]
+        samps[i] = sfft_sampler(SAMPLE_FN(), None, _ptr(f, C.c_int32), _ptr(c, C.c_double), f.shape[0],
+                                q.get("sigma", 0.0), q.get("noise_seed", q["seed"]), 0)
+    outs = (C.POINTER(sfft_result) * max(n, 1))()
+    status = (C.c_int * max(n, 1))()
+    rc = lib().sfft_dimincr_batch(params, samps, n, concurrency, outs, status)
+    try:
+        _check(rc)
+        return [_convert(outs[i].contents, problems[i]["d"]) for i in range(n)]
+    finally:
+        for i in range(n):
+            if outs[i]:
+                lib().sfft_free(outs[i])
 
 def prof_enable(on: bool = True) -> None:
     """Bracket every library kernel launch with CUDA events (see mr1l_prof_read)."""

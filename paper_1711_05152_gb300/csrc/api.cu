@@ -6,7 +6,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <memory>
+#include <thread>
 #include <vector>
 
 #include "ops.cuh"
@@ -755,34 +757,81 @@ struct SfftRun {
 
 }  // namespace mr1l
 
+static void validate_sfft(const sfft_params* params, const sfft_sampler* sampler) {
+  MR1L_REQUIRE(params && sampler, "null argument");
+  const sfft_params& P = *params;
+  MR1L_REQUIRE(P.d >= 2 && P.d <= SFFT_MAX_STEPS, "d must be in [2, 256]");
+  MR1L_REQUIRE(P.N >= 1 && P.N <= 2048, "N must be in [1, 2048]");
+  MR1L_REQUIRE(P.s >= 1 && P.s_local >= 1, "s and s_local must be >= 1");
+  MR1L_REQUIRE(P.r >= 1 && P.r <= 4096, "r must be in [1, 4096]");
+  MR1L_REQUIRE(P.b >= 1, "b must be >= 1");
+  MR1L_REQUIRE(P.theta >= 0.0 && std::isfinite(P.theta), "theta must be finite and >= 0");
+  MR1L_REQUIRE(P.theta_mode == SFFT_THETA_ABS || P.theta_mode == SFFT_THETA_REL, "bad theta_mode");
+  if (!sampler->fn) {
+    MR1L_REQUIRE(sampler->s >= 0, "planted s must be >= 0");
+    MR1L_REQUIRE(sampler->s == 0 || (sampler->freqs && sampler->coeffs), "planted arrays are null");
+    MR1L_REQUIRE(sampler->sigma >= 0.0, "sigma must be >= 0");
+    if (!sampler->device_arrays)
+      for (int64_t i = 0; i < sampler->s * P.d; ++i)
+        MR1L_REQUIRE(sampler->freqs[i] > -32768 && sampler->freqs[i] < 32768, "|h_j| must be < 2^15");
+  }
+}
+
+static sfft_result* run_one(const sfft_params& P, const sfft_sampler& S, cudaStream_t s) {
+  std::unique_ptr<SfftRun> run(new SfftRun());
+  run->P = P;
+  run->S = S;
+  run->s = s;
+  std::unique_ptr<sfft_result> res(new sfft_result());
+  std::memset(res.get(), 0, sizeof(sfft_result));
+  run->run(res.get());
+  return res.release();
+}
+
 extern "C" int sfft_dimincr(const sfft_params* params, const sfft_sampler* sampler, void* stream, sfft_result** out) {
   return guarded([&] {
-    MR1L_REQUIRE(params && sampler && out, "null argument");
+    MR1L_REQUIRE(out != nullptr, "null argument");
     *out = nullptr;
-    const sfft_params& P = *params;
-    MR1L_REQUIRE(P.d >= 2 && P.d <= SFFT_MAX_STEPS, "d must be in [2, 256]");
-    MR1L_REQUIRE(P.N >= 1 && P.N <= 2048, "N must be in [1, 2048]");
-    MR1L_REQUIRE(P.s >= 1 && P.s_local >= 1, "s and s_local must be >= 1");
-    MR1L_REQUIRE(P.r >= 1 && P.r <= 4096, "r must be in [1, 4096]");
-    MR1L_REQUIRE(P.b >= 1, "b must be >= 1");
-    MR1L_REQUIRE(P.theta >= 0.0 && std::isfinite(P.theta), "theta must be finite and >= 0");
-    MR1L_REQUIRE(P.theta_mode == SFFT_THETA_ABS || P.theta_mode == SFFT_THETA_REL, "bad theta_mode");
-    if (!sampler->fn) {
-      MR1L_REQUIRE(sampler->s >= 0, "planted s must be >= 0");
-      MR1L_REQUIRE(sampler->s == 0 || (sampler->freqs && sampler->coeffs), "planted arrays are null");
-      MR1L_REQUIRE(sampler->sigma >= 0.0, "sigma must be >= 0");
-      if (!sampler->device_arrays)
-        for (int64_t i = 0; i < sampler->s * P.d; ++i)
-          MR1L_REQUIRE(sampler->freqs[i] > -32768 && sampler->freqs[i] < 32768, "|h_j| must be < 2^15");
+    validate_sfft(params, sampler);
+    *out = run_one(*params, *sampler, (cudaStream_t)stream);
+  });
+}
+
+extern "C" int sfft_dimincr_batch(const sfft_params* params, const sfft_sampler* samplers, int count, int concurrency,
+                                  sfft_result** out, int* status) {
+  return guarded([&] {
+    MR1L_REQUIRE(count >= 0 && params && samplers && out && status, "null argument");
+    MR1L_REQUIRE(concurrency >= 1 && concurrency <= 256, "concurrency must be in [1, 256]");
+    for (int i = 0; i < count; ++i) {
+      out[i] = nullptr;
+      status[i] = MR1L_OK;
+      validate_sfft(params + i, samplers + i);
     }
-    std::unique_ptr<SfftRun> run(new SfftRun());
-    run->P = P;
-    run->S = *sampler;
-    run->s = (cudaStream_t)stream;
-    std::unique_ptr<sfft_result> res(new sfft_result());
-    std::memset(res.get(), 0, sizeof(sfft_result));
-    run->run(res.get());
-    *out = res.release();
+    int dev = 0;
+    MR1L_CUDA(cudaGetDevice(&dev));
+    // twiddle tables are built under a lock by whichever worker needs them first
+    const int workers = std::min(concurrency, std::max(count, 1));
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+      cudaSetDevice(dev);
+      cudaStream_t s = nullptr;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
+      for (;;) {
+        int i = next.fetch_add(1);
+        if (i >= count) break;
+        if (!s) {
+          status[i] = MR1L_E_CUDA;
+          continue;
+        }
+        status[i] = guarded([&] { out[i] = run_one(params[i], samplers[i], s); });
+      }
+      if (s) cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 0; w < workers; ++w) pool.emplace_back(worker);
+    for (auto& th : pool) th.join();
+    for (int i = 0; i < count; ++i)
+      if (status[i] != MR1L_OK) throw Error(status[i], "problem " + std::to_string(i) + " failed");
   });
 }
 
