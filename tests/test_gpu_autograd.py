@@ -39,7 +39,9 @@ def _fd_check(plan, y, c, ndir, h=1e-6, seed=0):
     for _ in range(ndir):
         v = torch.complex(torch.randn(y.shape, generator=gen, device=y.device, dtype=torch.float64),
                           torch.randn(y.shape, generator=gen, device=y.device, dtype=torch.float64))
-        v = v / v.abs().pow(2).sum().sqrt()
+        # direction scaled to |y|: the step h is relative to the point (the loss
+        # is exactly quadratic, so central differences carry only rounding)
+        v = v * (y.abs().pow(2).sum().sqrt() / v.abs().pow(2).sum().sqrt())
         fd = (_loss(plan, y + h * v, c) - _loss(plan, y - h * v, c)) / (2 * h)
         an = float(torch.real(torch.vdot(g.reshape(-1), v.reshape(-1))))
         worst = max(worst, abs(fd - an) / max(abs(an), 1e-30))
