@@ -137,6 +137,29 @@ int mr1l_reconstruct(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* 
  */
 int mr1l_evaluate(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode, void* stream);
 
+/*
+ * mr1l_reconstruct_noalloc - the same result as mr1l_reconstruct without any
+ * device allocation (the paper has no counterpart; this serves callers that
+ * cannot allocate device memory while they run: hosts whose device memory is
+ * owned entirely by another allocator or budget, and latency-critical loops
+ * that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+ * cause).  The caller still passes y and c exactly as for mr1l_reconstruct;
+ * the intermediate FFT data lives in one fixed scratch array compiled into
+ * the library (32 MiB per GPU that loads it, held until the process exits).
+ *   - Fails with MR1L_E_INVAL, naming both numbers, when nrhs * (sum_l M_l +
+ *     L * P) exceeds the fixed maximum of 2^21 complex elements (P is the
+ *     plan's Bluestein length, the power of two >= 2 max M_l - 1).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and must be serialised by the
+ *     caller.  No part of the array needs to start at zero.
+ *   - Allocates nothing on the device and calls no allocating routine (with
+ *     kernel profiling, mr1l_prof_enable, left off).
+ */
+int mr1l_reconstruct_noalloc(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 3                                                               */
 /* ------------------------------------------------------------------------ */

@@ -41,7 +41,7 @@ SFFT_MAX_STEPS = 256
 EXPORTS = [
     "mr1l_last_error", "mr1l_version", "mr1l_plan", "mr1l_plan_search", "mr1l_plan_info",
     "mr1l_plan_masks", "mr1l_destroy", "mr1l_reconstruct", "mr1l_evaluate", "sfft_dimincr",
-    "sfft_free", "sfft_dimincr_batch", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
+    "sfft_free", "sfft_dimincr_batch", "mr1l_reconstruct_noalloc", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
 ]
 
 
@@ -111,6 +111,7 @@ def lib() -> C.CDLL:
     L.mr1l_destroy.restype = None
     L.mr1l_reconstruct.argtypes = [vp, vp, C.c_int, vp, vp]
     L.mr1l_evaluate.argtypes = [vp, vp, C.c_int, vp, C.c_int, vp]
+    L.mr1l_reconstruct_noalloc.argtypes = [vp, vp, C.c_int, vp, vp]
     L.sfft_dimincr.argtypes = [C.POINTER(sfft_params), C.POINTER(sfft_sampler), vp,
                                C.POINTER(C.POINTER(sfft_result))]
     L.sfft_free.argtypes = [C.POINTER(sfft_result)]
@@ -202,6 +203,20 @@ class Plan:
         _check(lib().mr1l_reconstruct(self._h, C.c_void_p(y2.data_ptr()), nrhs, C.c_void_p(out.data_ptr()),
                                       C.c_void_p(_stream(stream))))
         return out[0] if squeeze else out
+
+    def reconstruct_noalloc(self, y, out, stream=None):
+        """Algorithm 2 like reconstruct, for callers that cannot allocate device
+        memory: the output tensor is required and the library's intermediate
+        data lives in its fixed scratch array (concurrent calls race)."""
+        import torch
+        y2 = y.reshape(-1, self.sum_M)
+        if y2.dtype != torch.complex128 or not y2.is_cuda or not y2.is_contiguous():
+            raise TypeError("y must be a contiguous complex128 CUDA tensor")
+        if out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous():
+            raise TypeError("out must be a contiguous complex128 CUDA tensor")
+        _check(lib().mr1l_reconstruct_noalloc(self._h, C.c_void_p(y2.data_ptr()), y2.shape[0],
+                                              C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream))))
+        return out
 
     def evaluate(self, c, mode: int = MR1L_EVAL, out=None, stream=None):
         """Lattice evaluation (mode MR1L_EVAL) or the adjoint of Algorithm 2

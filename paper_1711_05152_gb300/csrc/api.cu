@@ -8,6 +8,7 @@
 #include <cstring>
 #include <atomic>
 #include <memory>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -840,4 +841,77 @@ extern "C" void sfft_free(sfft_result* res) {
   std::free(res->freqs);
   std::free(res->coeffs);
   delete res;
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction without allocation.
+//
+// Some callers cannot allocate device memory while they run: hosts whose
+// device memory is entirely owned by another allocator (a framework's caching
+// allocator that has reserved the GPU, a fixed memory budget), and
+// latency-critical loops that cannot afford the device-wide synchronisation
+// cudaMalloc / cudaFree may cause.  mr1l_reconstruct grows plan-owned scratch
+// on demand; this variant instead uses a fixed scratch array compiled into the
+// library.  Every GPU that loads the library holds that array (32 MiB) until
+// the process exits.
+// ---------------------------------------------------------------------------
+namespace mr1l {
+
+constexpr int64_t kNoallocScratchElems = int64_t(1) << 21;  // complex128 elements = 32 MiB
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) cplx g_noalloc_scratch[kNoallocScratchElems];
+
+static std::mutex g_noalloc_mu;
+static cplx* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the symbol is only a host-side stand-in, so the address is looked up once
+// per device, with that device current.
+static cplx* noalloc_scratch() {
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  MR1L_REQUIRE(dev >= 0 && dev < kNoallocMaxDevices, "device index out of range for the fixed scratch");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      throw Error(MR1L_E_CUDA, std::string("cudaGetSymbolAddress(fixed scratch): ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = (cplx*)ptr;
+  }
+  return g_noalloc_addr[dev];
+}
+
+}  // namespace mr1l
+
+extern "C" int mr1l_reconstruct_noalloc(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* stream) {
+  return guarded([&] {
+    MR1L_REQUIRE(plan != nullptr, "plan is null");
+    MR1L_REQUIRE(nrhs >= 0 && nrhs <= 65535 / 64, "nrhs out of range");
+    if (nrhs == 0) return;
+    MR1L_REQUIRE(y != nullptr && c != nullptr, "null array");
+    MR1L_REQUIRE(((uintptr_t)y & 15) == 0 && ((uintptr_t)c & 15) == 0, "arrays must be 16-byte aligned");
+    LatticeWork& lw = plan->lw;
+    const int64_t sumM = lw.sumM;
+    const int64_t need = (int64_t)nrhs * (sumM + (int64_t)lw.Luse * lw.geom.P);
+    if (need > kNoallocScratchElems)
+      throw Error(MR1L_E_INVAL, "mr1l_reconstruct_noalloc needs " + std::to_string(need) +
+                                    " complex scratch elements (nrhs * (sum M + L * P)); the fixed maximum is " +
+                                    std::to_string(kNoallocScratchElems));
+    cudaStream_t s = (cudaStream_t)stream;
+    cplx* scratch = noalloc_scratch();
+    // C needs no clearing: every entry the gather reads is written first
+    cplx* Cbuf = scratch;
+    cplx* work = scratch + (size_t)nrhs * sumM;
+    BlueIO io{};
+    io.in = (const cplx*)y;
+    io.in_stride = sumM;
+    io.out = Cbuf;
+    io.out_stride = sumM;
+    io.work = work;
+    blue_run(lw.geom, io, kModeRecon, nrhs, s);
+    gather(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, Cbuf, sumM, nrhs, (cplx*)c, plan->nI,
+           nullptr, nullptr, s);
+  });
 }
