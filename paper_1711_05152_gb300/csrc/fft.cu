@@ -83,6 +83,36 @@ struct RegDft<8, INV> {
   }
 };
 
+// Radix-8 DFT of a sequence whose inputs 4..7 are zero (the first stage of a
+// zero-padded Bluestein input): v[0..3] in, v[0..7] out, 40 FP64 operations
+// instead of 56.
+template <bool INV>
+__device__ __forceinline__ void reg_dft8_half(cplx* v) {
+  const double h = 0.70710678118654752440;
+  cplx e0 = cadd(v[0], v[2]), e2 = csub(v[0], v[2]);
+  cplx m2 = mul_mi<INV>(v[2]);
+  cplx e1 = cadd(v[0], m2), e3 = csub(v[0], m2);
+  cplx o0 = cadd(v[1], v[3]), o2 = csub(v[1], v[3]);
+  cplx m3 = mul_mi<INV>(v[3]);
+  cplx o1 = cadd(v[1], m3), o3 = csub(v[1], m3);
+  if (!INV) {
+    o1 = cmake((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+    o3 = cmake((o3.y - o3.x) * h, -(o3.x + o3.y) * h);
+  } else {
+    o1 = cmake((o1.x - o1.y) * h, (o1.x + o1.y) * h);
+    o3 = cmake(-(o3.x + o3.y) * h, (o3.x - o3.y) * h);
+  }
+  o2 = mul_mi<INV>(o2);
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
 // ---------------------------------------------------------------------------
 // One Stockham stage of radix R over nseq sequences of length n in shared
 // memory; element i of sequence b sits at s[b * bs + i * is].  Every thread
@@ -91,7 +121,8 @@ struct RegDft<8, INV> {
 //   COLS: sequence index fastest across threads (column tiles, bs == 1)
 //   else: element index fastest (row tiles, is == 1)
 // ---------------------------------------------------------------------------
-template <int R, bool INV, bool COLS>
+// HALF (first radix-8 stage only): inputs r >= 4 are known zeros.
+template <int R, bool INV, bool COLS, bool HALF = false>
 __device__ __forceinline__ void stockham_stage(cplx* s, int n, int lognb, int Ns, int nseq, int bs,
                                                int is, const cplx* twn_n) {
   constexpr int CNT = 8 / R;
@@ -114,7 +145,12 @@ __device__ __forceinline__ void stockham_stage(cplx* s, int n, int lognb, int Ns
     }
     int k = j & (Ns - 1);
     base[c] = b * bs + ((j - k) * R + k) * is;
-    if (act[c]) {
+    if (act[c] && HALF) {
+      const cplx* src = s + b * bs + j * is;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) v[c][r] = src[r * nb * is];
+      reg_dft8_half<INV>(v[c]);
+    } else if (act[c]) {
       const cplx* src = s + b * bs + j * is;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[c][r] = src[r * nb * is];
@@ -142,11 +178,17 @@ __device__ __forceinline__ void stockham_stage(cplx* s, int n, int lognb, int Ns
 
 // Full in-smem FFT of length n = 2^logn (radix-8 stages, then one radix-4 or
 // radix-2 stage).  Natural order in and out.
-template <bool INV, bool COLS>
+// HALF_FIRST: the upper half of every input sequence is zero (needs logn >= 3).
+template <bool INV, bool COLS, bool HALF_FIRST = false>
 __device__ __forceinline__ void smem_fft(cplx* s, int n, int logn, int nseq, int bs, int is,
                                          const cplx* twn) {
   const cplx* twn_n = twn + n;
   int Ns = 1, rem = logn;
+  if (HALF_FIRST && rem >= 3) {
+    stockham_stage<8, INV, COLS, true>(s, n, logn - 3, Ns, nseq, bs, is, twn_n);
+    Ns <<= 3;
+    rem -= 3;
+  }
   while (rem >= 3) {
     stockham_stage<8, INV, COLS>(s, n, logn - 3, Ns, nseq, bs, is, twn_n);
     Ns <<= 3;
@@ -210,9 +252,16 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
   const int l = gi % g.L, h = gi / g.L;
   const int P = g.P, M = g.M[l];
   const int64_t off = g.off[l];
-  for (int n = threadIdx.x; n < P; n += blockDim.x) sm[n] = load_input<MODE>(g, io, l, h, M, off, n);
+  // zero padding: for RECON / EVAL the input vanishes from M <= P/2 on, so the
+  // upper half is never loaded and the first radix-8 stage skips it
+  const bool half = MODE != kModeFilter && g.logP >= 3;
+  const int nload = half ? P / 2 : P;
+  for (int n = threadIdx.x; n < nload; n += blockDim.x) sm[n] = load_input<MODE>(g, io, l, h, M, off, n);
   __syncthreads();
-  smem_fft<false, false>(sm, P, g.logP, 1, 0, 1, g.twn);
+  if (half)
+    smem_fft<false, false, true>(sm, P, g.logP, 1, 0, 1, g.twn);
+  else
+    smem_fft<false, false>(sm, P, g.logP, 1, 0, 1, g.twn);
   cplx* Bh = g.Bh + (int64_t)l * P;
   if (MODE == kModeFilter) {
     const double sc = 1.0 / (double)P;  // exact: P is a power of two
@@ -228,12 +277,16 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
 // ---------------------------------------------------------------------------
 // 4-step passes
 // ---------------------------------------------------------------------------
+// Tiles of 2048 complex (32 KB shared memory, 256 threads) so that three CTAs
+// share an SM and hide each other's load and barrier phases; a single
+// column or row of 4096 takes a 4096-element tile.
+constexpr int kTileElems = 2048;
 __host__ __device__ __forceinline__ int col_tile(int P1) {
-  int cb = 4096 / P1;
+  int cb = kTileElems / P1;
   return cb > 16 ? 16 : (cb < 1 ? 1 : cb);
 }
 __host__ __device__ __forceinline__ int row_tile(int P2) {
-  int rb = 4096 / P2;
+  int rb = kTileElems / P2;
   return rb < 1 ? 1 : rb;
 }
 
@@ -248,12 +301,17 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
   const int M = g.M[l];
   const int64_t off = g.off[l];
   const int n2_0 = blockIdx.x * CB;
-  for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
+  // RECON / EVAL: rows n1 >= P1/2 hold n >= P/2 >= M, i.e. zero padding
+  const int rows = MODE == kModeFilter ? P1 : P1 / 2;
+  for (int e = threadIdx.x; e < rows * CB; e += blockDim.x) {
     int i = e / CB, b = e - i * CB;
     sm[e] = load_input<MODE>(g, io, l, h, M, off, (int64_t)i * P2 + n2_0 + b);
   }
   __syncthreads();
-  smem_fft<false, true>(sm, P1, logP1, CB, 1, CB, g.twn);
+  if (MODE == kModeFilter)
+    smem_fft<false, true>(sm, P1, logP1, CB, 1, CB, g.twn);
+  else
+    smem_fft<false, true, true>(sm, P1, logP1, CB, 1, CB, g.twn);
   cplx* work = io.work + (int64_t)gi * P;
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int k1 = e / CB, b = e - k1 * CB;
