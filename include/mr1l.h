@@ -219,6 +219,9 @@ typedef struct sfft_params {
     int theta_mode;         /* SFFT_THETA_ABS or SFFT_THETA_REL */
     uint64_t seed;          /* Philox key of anchors and generating vectors */
     int batch_reps;         /* 0: one repetition per launch sequence; 1: all r~ fused */
+    int t_stop;             /* 0: all d increments; 2 <= t_stop < d: stop after increment t_stop
+                               and return the projected set I^(1..t_stop) (rows of t_stop
+                               components, coefficients zero) - a bounded prefix of the run */
 } sfft_params;
 
 #define SFFT_MAX_STEPS 256

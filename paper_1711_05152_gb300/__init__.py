@@ -69,7 +69,7 @@ class sfft_sampler(C.Structure):
 class sfft_params(C.Structure):
     _fields_ = [("d", C.c_int), ("N", C.c_int), ("s", C.c_int64), ("s_local", C.c_int64),
                 ("r", C.c_int), ("b", C.c_int), ("theta", C.c_double), ("theta_mode", C.c_int),
-                ("seed", C.c_uint64), ("batch_reps", C.c_int)]
+                ("seed", C.c_uint64), ("batch_reps", C.c_int), ("t_stop", C.c_int)]
 
 
 class sfft_step_stats(C.Structure):
@@ -285,13 +285,13 @@ class SfftOutput:
 def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str = "rel", seed: int = 0,
                  s_local: int | None = None, b: int = 10, freqs=None, coeffs=None, sigma: float = 0.0,
                  noise_seed: int | None = None, sampler=None, batch_reps: bool = False,
-                 stream=None) -> SfftOutput:
+                 t_stop: int | None = None, stream=None) -> SfftOutput:
     """Algorithm 3.  Either a planted polynomial (freqs [s, d], coeffs [s],
     sigma) evaluated by the library, or ``sampler(req, y_ptr, stream_ptr)``,
     a Python callable that fills the device buffer y_ptr for a request."""
     p = sfft_params(d=d, N=N, s=s, s_local=s if s_local is None else s_local, r=r, b=b, theta=theta,
                     theta_mode=SFFT_THETA_REL if theta_mode == "rel" else SFFT_THETA_ABS, seed=seed,
-                    batch_reps=1 if batch_reps else 0)
+                    batch_reps=1 if batch_reps else 0, t_stop=t_stop or 0)
     keep = []
     nseed = seed if noise_seed is None else noise_seed
     if sampler is None and getattr(freqs, "is_cuda", False):
@@ -324,13 +324,13 @@ def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str =
     out = C.POINTER(sfft_result)()
     _check(lib().sfft_dimincr(C.byref(p), C.byref(samp), C.c_void_p(_stream(stream)), C.byref(out)))
     try:
-        return _convert(out.contents, d)
+        return _convert(out.contents)
     finally:
         lib().sfft_free(out)
 
 
-def _convert(res: sfft_result, d: int) -> SfftOutput:
-    n = res.n
+def _convert(res: sfft_result) -> SfftOutput:
+    n, d = res.n, res.d
     fr = np.ctypeslib.as_array(res.freqs, shape=(max(n, 1) * d,))[: n * d].astype(np.int64).reshape(n, d)
     cf = np.ctypeslib.as_array(res.coeffs, shape=(max(n, 1) * 2,))[: 2 * n].copy().view(np.complex128)
     st = res.stats
@@ -366,7 +366,7 @@ def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[Sfft
     rc = lib().sfft_dimincr_batch(params, samps, n, concurrency, outs, status)
     try:
         _check(rc)
-        return [_convert(outs[i].contents, problems[i]["d"]) for i in range(n)]
+        return [_convert(outs[i].contents) for i in range(n)]
     finally:
         for i in range(n):
             if outs[i]:

@@ -733,6 +733,7 @@ struct SfftRun {
       }
       MR1L_CUDA(cudaStreamSynchronize(s));
       st.n_detected = np;
+      if (P.t_stop && t == P.t_stop) break;
     }
     MR1L_CUDA(cudaStreamSynchronize(s));
     double samp = 0.0;
@@ -743,14 +744,15 @@ struct SfftRun {
     }
     stats.ms_sampling = samp;
     stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const int dout = tp;  // d, or t_stop for a run stopped early
     res->n = np;
-    res->d = d;
-    res->freqs = (int32_t*)std::malloc(std::max<int64_t>(np * d, 1) * sizeof(int32_t));
-    res->coeffs = (double*)std::malloc(std::max<int64_t>(np, 1) * 2 * sizeof(double));
+    res->d = dout;
+    res->freqs = (int32_t*)std::malloc(std::max<int64_t>(np * dout, 1) * sizeof(int32_t));
+    res->coeffs = (double*)std::calloc(std::max<int64_t>(np, 1) * 2, sizeof(double));
     if (!res->freqs || !res->coeffs) throw std::bad_alloc();
     if (np) {
-      std::memcpy(res->freqs, pre_h.data(), np * d * sizeof(int32_t));
-      std::memcpy(res->coeffs, coef_h.data(), np * sizeof(cplx));
+      std::memcpy(res->freqs, pre_h.data(), np * dout * sizeof(int32_t));
+      if ((int64_t)coef_h.size() == np) std::memcpy(res->coeffs, coef_h.data(), np * sizeof(cplx));
     }
     res->stats = stats;
   }
@@ -768,6 +770,7 @@ static void validate_sfft(const sfft_params* params, const sfft_sampler* sampler
   MR1L_REQUIRE(P.b >= 1, "b must be >= 1");
   MR1L_REQUIRE(P.theta >= 0.0 && std::isfinite(P.theta), "theta must be finite and >= 0");
   MR1L_REQUIRE(P.theta_mode == SFFT_THETA_ABS || P.theta_mode == SFFT_THETA_REL, "bad theta_mode");
+  MR1L_REQUIRE(P.t_stop == 0 || (P.t_stop >= 2 && P.t_stop <= P.d), "t_stop must be 0 or in [2, d]");
   if (!sampler->fn) {
     MR1L_REQUIRE(sampler->s >= 0, "planted s must be >= 0");
     MR1L_REQUIRE(sampler->s == 0 || (sampler->freqs && sampler->coeffs), "planted arrays are null");
