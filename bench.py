@@ -123,6 +123,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_scalar(x: float, op: str, world: int, device=None) -> float:
+    """Across ranks: "max" (the slowest rank's time) or "sum" (all ranks'
+    units).  A no-op for one rank; uses the default process group otherwise."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -218,11 +230,7 @@ def run_ours(args):
             torch.distributed.barrier()
 
     def reduce(x, op):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=op)
-        return float(t.item())
+        return reduce_scalar(x, op, world, dev)
 
     def timed(batch, profile):
         for _ in range(args.warmup):
@@ -250,9 +258,8 @@ def run_ours(args):
         if profile:
             P.prof_enable(False)
             prof = P.prof_read()
-        import torch.distributed as dist_mod
-        max_ms = reduce(total_ms, dist_mod.ReduceOp.MAX if world > 1 else None)
-        all_det = reduce(float(detected), dist_mod.ReduceOp.SUM if world > 1 else None)
+        max_ms = reduce(total_ms, "max")
+        all_det = reduce(float(detected), "sum")
         return dict(ms=max_ms, detected=all_det, launches=launches, prof=prof, last=last)
 
     clocks = ClockSampler(local)
@@ -270,9 +277,8 @@ def run_ours(args):
         out = solve(True, host=True)
         det_e2e += out.freqs.shape[0]
     e2e_s = time.perf_counter() - t0
-    import torch.distributed as dist_mod
-    e2e_s = reduce(e2e_s, dist_mod.ReduceOp.MAX if world > 1 else None)
-    det_e2e = reduce(float(det_e2e), dist_mod.ReduceOp.SUM if world > 1 else None)
+    e2e_s = reduce(e2e_s, "max")
+    det_e2e = reduce(float(det_e2e), "sum")
     h2d = sig.freqs.size * 4 + sig.coeffs.size * 16
     d2h = int(out.freqs.size * 4 + out.coeffs.size * 16)
 
