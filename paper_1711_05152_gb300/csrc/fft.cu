@@ -65,27 +65,36 @@ struct RegDft<8, INV> {
     cplx o[4] = {v[1], v[3], v[5], v[7]};
     RegDft<4, INV>::run(e);
     RegDft<4, INV>::run(o);
-    // o1 *= w8, o2 *= w8^2 = -+i, o3 *= w8^3
+    // X_k = E_k + w8^k O_k, X_{k+4} = E_k - w8^k O_k; the 1/sqrt(2) of w8 and
+    // w8^3 is folded into fused multiply-adds
     cplx a = o[1], c = o[3];
+    double a1x, a1y, a3x, a3y;  // w8 O_1 and w8^3 O_3 without the factor h
     if (!INV) {
-      o[1] = cmake((a.x + a.y) * h, (a.y - a.x) * h);
-      o[3] = cmake((c.y - c.x) * h, -(c.x + c.y) * h);
+      a1x = a.x + a.y;
+      a1y = a.y - a.x;
+      a3x = c.y - c.x;
+      a3y = -(c.x + c.y);
     } else {
-      o[1] = cmake((a.x - a.y) * h, (a.x + a.y) * h);
-      o[3] = cmake(-(c.x + c.y) * h, (c.x - c.y) * h);
+      a1x = a.x - a.y;
+      a1y = a.x + a.y;
+      a3x = -(c.x + c.y);
+      a3y = c.x - c.y;
     }
-    o[2] = mul_mi<INV>(o[2]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      v[k] = cadd(e[k], o[k]);
-      v[k + 4] = csub(e[k], o[k]);
-    }
+    cplx o2 = mul_mi<INV>(o[2]);
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cmake(fma(h, a1x, e[1].x), fma(h, a1y, e[1].y));
+    v[5] = cmake(fma(-h, a1x, e[1].x), fma(-h, a1y, e[1].y));
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cmake(fma(h, a3x, e[3].x), fma(h, a3y, e[3].y));
+    v[7] = cmake(fma(-h, a3x, e[3].x), fma(-h, a3y, e[3].y));
   }
 };
 
 // Radix-8 DFT of a sequence whose inputs 4..7 are zero (the first stage of a
-// zero-padded Bluestein input): v[0..3] in, v[0..7] out, 40 FP64 operations
-// instead of 56.
+// zero-padded Bluestein input): v[0..3] in, v[0..7] out, 36 FP64 operations
+// instead of 52.
 template <bool INV>
 __device__ __forceinline__ void reg_dft8_half(cplx* v) {
   const double h = 0.70710678118654752440;
@@ -95,22 +104,27 @@ __device__ __forceinline__ void reg_dft8_half(cplx* v) {
   cplx o0 = cadd(v[1], v[3]), o2 = csub(v[1], v[3]);
   cplx m3 = mul_mi<INV>(v[3]);
   cplx o1 = cadd(v[1], m3), o3 = csub(v[1], m3);
+  double a1x, a1y, a3x, a3y;
   if (!INV) {
-    o1 = cmake((o1.x + o1.y) * h, (o1.y - o1.x) * h);
-    o3 = cmake((o3.y - o3.x) * h, -(o3.x + o3.y) * h);
+    a1x = o1.x + o1.y;
+    a1y = o1.y - o1.x;
+    a3x = o3.y - o3.x;
+    a3y = -(o3.x + o3.y);
   } else {
-    o1 = cmake((o1.x - o1.y) * h, (o1.x + o1.y) * h);
-    o3 = cmake(-(o3.x + o3.y) * h, (o3.x - o3.y) * h);
+    a1x = o1.x - o1.y;
+    a1y = o1.x + o1.y;
+    a3x = -(o3.x + o3.y);
+    a3y = o3.x - o3.y;
   }
   o2 = mul_mi<INV>(o2);
   v[0] = cadd(e0, o0);
   v[4] = csub(e0, o0);
-  v[1] = cadd(e1, o1);
-  v[5] = csub(e1, o1);
+  v[1] = cmake(fma(h, a1x, e1.x), fma(h, a1y, e1.y));
+  v[5] = cmake(fma(-h, a1x, e1.x), fma(-h, a1y, e1.y));
   v[2] = cadd(e2, o2);
   v[6] = csub(e2, o2);
-  v[3] = cadd(e3, o3);
-  v[7] = csub(e3, o3);
+  v[3] = cmake(fma(h, a3x, e3.x), fma(h, a3y, e3.y));
+  v[7] = cmake(fma(-h, a3x, e3.x), fma(-h, a3y, e3.y));
 }
 
 // ---------------------------------------------------------------------------

@@ -72,6 +72,9 @@ void detect_lines(const cplx* y, int nlines, int N, int64_t cap, double theta2, 
                   cudaStream_t s);
 
 // Selection state of one segment (device memory, see select.cu).
+constexpr int kSelBits = 11;                 // radix digit width
+constexpr int kSelBins = 1 << kSelBits;
+constexpr int kSelPasses = 6;                // digits [52,63) [41,52) [30,41) [19,30) [8,19) [0,8)
 struct SelectState {
   uint64_t thr;        // squared-threshold bits
   uint64_t prefix;     // radix-select prefix
@@ -79,7 +82,8 @@ struct SelectState {
   int64_t total;       // eligible count (keys >= thr)
   int take_all;        // eligible count <= cap
   int64_t eq_count;    // keys equal to the final prefix
-  uint32_t hist[256];
+  unsigned int ticket; // CTAs of the current histogram pass that have finished
+  uint32_t hist[kSelBins];
 };
 
 // Thresholded "(up to) cap largest" over nrhs segments of n keys each

@@ -3,9 +3,9 @@
 //
 // Keys are bits(|p~|^2) + 1 for covered candidates and 0 otherwise; for
 // non-negative doubles the bit pattern orders like the value, so the
-// selection is an integer radix select: eight passes of an 8-bit digit
-// histogram (multi-CTA, shared-memory privatised) each followed by a one-CTA
-// pick, then a marking pass.  Ties at the cut are broken by the smaller
+// selection is an integer radix select: six passes of an 11-bit digit
+// histogram (multi-CTA, shared-memory privatised), the last CTA of each pass
+// picking the digit, then a marking pass.  Ties at the cut are broken by the smaller
 // candidate id, as the (lexicographic) candidate order demands.
 #include "ops.cuh"
 #include "prof.cuh"
@@ -13,71 +13,120 @@
 namespace mr1l {
 
 __global__ void sel_init_kernel(SelectState* st, const uint64_t* keymax, double theta2, int rel, int nrhs) {
-  int h = blockIdx.x * blockDim.x + threadIdx.x;
+  int h = blockIdx.x;
   if (h >= nrhs) return;
-  double thr = theta2;
-  if (rel) {
-    uint64_t km = keymax[h];
-    double mx = km ? __longlong_as_double((long long)(km - 1)) : 0.0;
-    thr = theta2 * mx;
-  }
   SelectState& S = st[h];
-  S.thr = (uint64_t)__double_as_longlong(thr) + 1;  // covered keys carry +1
-  S.prefix = 0;
-  S.need = 0;
-  S.total = 0;
-  S.take_all = 0;
-  S.eq_count = 0;
-  for (int i = 0; i < 256; ++i) S.hist[i] = 0;
+  if (threadIdx.x == 0) {
+    double thr = theta2;
+    if (rel) {
+      uint64_t km = keymax[h];
+      double mx = km ? __longlong_as_double((long long)(km - 1)) : 0.0;
+      thr = theta2 * mx;
+    }
+    S.thr = (uint64_t)__double_as_longlong(thr) + 1;  // covered keys carry +1
+    S.prefix = 0;
+    S.need = 0;
+    S.total = 0;
+    S.take_all = 0;
+    S.eq_count = 0;
+    S.ticket = 0;
+  }
+  for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) S.hist[i] = 0;
 }
 
-__global__ void sel_hist_kernel(const uint64_t* keys, int64_t n, SelectState* st, int pass) {
-  __shared__ uint32_t hist[256];
+__device__ __forceinline__ void sel_digit(int pass, int& lo, int& width) {
+  // digits from the top: [52,63) [41,52) [30,41) [19,30) [8,19) [0,8)
+  lo = pass < kSelPasses - 1 ? 52 - 11 * pass : 0;
+  width = pass < kSelPasses - 1 ? 11 : 8;
+}
+
+// The last CTA of a histogram pass picks the digit of the cap-th largest key:
+// a parallel suffix scan over the bins (256 threads, 8 bins each).
+__device__ void sel_pick(SelectState& S, int64_t cap, int pass) {
+  __shared__ int64_t part[256];
+  __shared__ int64_t cum_above[256];
+  int lo, width;
+  sel_digit(pass, lo, width);
+  const int nb = 1 << width;
+  const int per = (nb + blockDim.x - 1) / blockDim.x;
+  // thread i owns bins [i*per, (i+1)*per); scan from the highest bin down
+  const int t = threadIdx.x;
+  int64_t mine = 0;
+  for (int k = 0; k < per; ++k) {
+    int b = t * per + k;
+    if (b < nb) mine += S.hist[b];
+  }
+  part[t] = mine;
+  __syncthreads();
+  if (t == 0) {
+    int64_t tot = 0;
+    for (int i = blockDim.x - 1; i >= 0; --i) {
+      cum_above[i] = tot;
+      tot += part[i];
+    }
+    if (pass == 0) {
+      S.total = tot;
+      if (tot <= cap) S.take_all = 1;
+      else S.need = cap;
+    }
+  }
+  __syncthreads();
+  if (!S.take_all) {
+    const int64_t need = S.need;
+    // exactly one thread's range contains the crossing
+    if (cum_above[t] < need && cum_above[t] + part[t] >= need) {
+      int64_t cum = cum_above[t];
+      for (int k = per - 1; k >= 0; --k) {
+        int b = t * per + k;
+        if (b >= nb) continue;
+        int64_t hc = S.hist[b];
+        if (cum + hc >= need) {
+          S.prefix |= (uint64_t)b << lo;
+          S.need = need - cum;
+          S.eq_count = hc;
+          break;
+        }
+        cum += hc;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = t; i < nb; i += blockDim.x) S.hist[i] = 0;
+  if (t == 0) S.ticket = 0;
+}
+
+__global__ void __launch_bounds__(256) sel_hist_kernel(const uint64_t* keys, int64_t n, SelectState* st, int pass,
+                                                       int64_t cap) {
+  __shared__ uint32_t hist[kSelBins];
+  __shared__ bool last;
   const int h = blockIdx.y;
   SelectState& S = st[h];
-  if (S.take_all) return;
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+  if (S.take_all) return;  // uniform per segment
+  int lo, width;
+  sel_digit(pass, lo, width);
+  const int nb = 1 << width;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
   __syncthreads();
-  const int shift = 56 - 8 * pass;
   const uint64_t thr = S.thr;
-  const uint64_t hi_mask = pass == 0 ? 0ull : (~0ull << (shift + 8));
+  const uint64_t hi_mask = pass == 0 ? 0ull : (~0ull << (lo + width));
   const uint64_t prefix = S.prefix & hi_mask;
   const uint64_t* kh = keys + h * n;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
     uint64_t k = kh[c];
-    if (k >= thr && (k & hi_mask) == prefix) atomicAdd(&hist[(k >> shift) & 255], 1u);
+    if (k >= thr && (k & hi_mask) == prefix) atomicAdd(&hist[(k >> lo) & (nb - 1)], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
     if (hist[i]) atomicAdd(&S.hist[i], hist[i]);
-}
-
-__global__ void sel_pick_kernel(SelectState* st, int64_t cap, int pass) {
-  SelectState& S = st[blockIdx.x];
-  if (threadIdx.x != 0 || S.take_all) return;
-  const int shift = 56 - 8 * pass;
-  if (pass == 0) {
-    int64_t tot = 0;
-    for (int i = 0; i < 256; ++i) tot += S.hist[i];
-    S.total = tot;
-    if (tot <= cap) {
-      S.take_all = 1;
-      return;
-    }
-    S.need = cap;
+  // last CTA of this segment picks the digit
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&S.ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    sel_pick(S, cap, pass);
   }
-  int64_t cum = 0;
-  for (int dgt = 255; dgt >= 0; --dgt) {
-    int64_t hcount = S.hist[dgt];
-    if (cum + hcount >= S.need) {
-      S.prefix |= (uint64_t)dgt << shift;
-      S.need -= cum;
-      S.eq_count = hcount;
-      break;
-    }
-    cum += hcount;
-  }
-  for (int i = 0; i < 256; ++i) S.hist[i] = 0;
 }
 
 __global__ void sel_mark_kernel(const uint64_t* keys, int64_t n, const SelectState* st, uint8_t* flags) {
@@ -128,12 +177,11 @@ __global__ void sel_tie_kernel(const uint64_t* keys, int64_t n, const SelectStat
 void select_topk(const uint64_t* keys, int64_t n, int nrhs, const uint64_t* keymax, double theta2, int rel,
                  int64_t cap, SelectState* st, uint8_t* flags, cudaStream_t s) {
   if (n == 0 || nrhs == 0) return;
-  MR1L_LAUNCH("sel_init_kernel", s, 0, 0, sel_init_kernel<<<cdiv(nrhs, 64), 64, 0, s>>>(st, keymax, theta2, rel, nrhs));
-  int blocks = (int)std::min<int64_t>(cdiv(n, 1024), 304);
-  for (int pass = 0; pass < 8; ++pass) {
-    MR1L_LAUNCH("sel_hist_kernel", s, 0, 0, sel_hist_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, pass));
-    MR1L_LAUNCH("sel_pick_kernel", s, 0, 0, sel_pick_kernel<<<nrhs, 32, 0, s>>>(st, cap, pass));
-  }
+  MR1L_LAUNCH("sel_init_kernel", s, 0, 0, sel_init_kernel<<<nrhs, 256, 0, s>>>(st, keymax, theta2, rel, nrhs));
+  int blocks = (int)std::min<int64_t>(cdiv(n, 2048), 304);
+  for (int pass = 0; pass < kSelPasses; ++pass)
+    MR1L_LAUNCH("sel_hist_kernel", s, 0, 8.0 * n * nrhs,
+                sel_hist_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, pass, cap));
   MR1L_LAUNCH("sel_mark_kernel", s, 0, 0, sel_mark_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, flags));
   MR1L_LAUNCH("sel_tie_kernel", s, 0, 0, sel_tie_kernel<<<nrhs, 1024, 0, s>>>(keys, n, st, flags));
 }
