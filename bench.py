@@ -43,10 +43,63 @@ import workloads as W
 METRIC = "detected coeffs/sec & lattice-transform HBM GB/s (% peak), batched vs plain, same GB300"
 UNIT = "coeffs/s"
 WORKLOAD = "plain_d10"
-CONFIG = {
-    "workload": "plain_d10: d=10, N=32 (box [-32,32]^10), s=1000 planted, |c|~U[1,10] uniform phase, "
-                "SNR 40 dB, r=5, theta=1e-12 relative, b=10",
+DESCRIPTIONS = {
+    "plain_d10": "plain_d10: d=10, N=32 (box [-32,32]^10), s=1000 planted, |c|~U[1,10] uniform phase, "
+                 "SNR 40 dB, r=5, theta=1e-12 relative, b=10",
+    "large_d25": "large_d25: d=25, N=32, s=10000 planted, |c| log-uniform in [1e-2,10], SNR 20 dB, r=10, "
+                 "theta=1e-12 relative, b=10",
+    "batch256": "batch256: 256 independent noiseless signals, d~U{5..12}, N in {16,32,64}, s log-uniform "
+                "in [100,2000], r=3, theta=1e-12 relative, b=10",
 }
+FORMS = {
+    "plain_d10": ("batched: the r repetitions of an increment fused in each launch",
+                  "plain: one repetition per launch sequence"),
+    "large_d25": ("batched: the r repetitions of an increment fused in each launch",
+                  "plain: one repetition per launch sequence"),
+    "batch256": ("batched: 16 signals in flight on their own streams, repetitions fused",
+                 "plain: one signal after another on one stream, one repetition per launch sequence"),
+}
+CONFIG = {"workload": DESCRIPTIONS[WORKLOAD]}
+
+
+class Workload:
+    """Planted inputs of a named workload and its two GPU forms."""
+
+    def __init__(self, name: str, seed: int, dev):
+        import torch
+        self.name = name
+        if name == "batch256":
+            self.items = W.batch_signals(256, seed)
+        else:
+            self.items = [W.workload(name, seed)]
+        self.seeds = [seed * 1000 + i if name == "batch256" else seed for i in range(len(self.items))]
+        self.dev_arrays = [(torch.from_numpy(np.ascontiguousarray(sig.freqs, dtype=np.int32)).to(dev),
+                            torch.from_numpy(np.ascontiguousarray(sig.coeffs)).to(dev)) for sig, _ in self.items]
+
+    def problems(self, host: bool, batched: bool):
+        out = []
+        for (sig, p), sd, (fd, cd) in zip(self.items, self.seeds, self.dev_arrays):
+            out.append(dict(d=sig.d, N=sig.N, s=p["s"], s_local=p["s_local"], r=p["r"], b=p["b"],
+                            theta=p["theta"], theta_mode=p["theta_mode"], seed=sd,
+                            freqs=sig.freqs if host else fd, coeffs=sig.coeffs if host else cd,
+                            sigma=sig.sigma, batch_reps=batched))
+        return out
+
+    def solve(self, batched: bool, host: bool = False):
+        import paper_1711_05152_gb300 as P
+        probs = self.problems(host, batched)
+        if self.name == "batch256" and batched:
+            return P.sfft_dimincr_batch(probs, concurrency=16)
+        outs = []
+        for q in probs:
+            outs.append(P.sfft_dimincr(q["d"], q["N"], q["s"], q["r"], q["theta"], q["theta_mode"], seed=q["seed"],
+                                       s_local=q["s_local"], b=q["b"], freqs=q["freqs"], coeffs=q["coeffs"],
+                                       sigma=q["sigma"], batch_reps=batched))
+        return outs
+
+    def exact(self, outs) -> bool:
+        return all(set(map(tuple, o.freqs.tolist())) == set(map(tuple, sig.freqs.astype(int).tolist()))
+                   for o, (sig, _) in zip(outs, self.items))
 # FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz max SM clock
 SM_COUNT, FP64_FMA_PER_CLK, SM_MAX_GHZ = 152, 2, 2.070
 FP64_PEAK_TFLOPS = SM_COUNT * FP64_FMA_PER_CLK * 2 * SM_MAX_GHZ / 1e3
@@ -146,20 +199,38 @@ def _dist():
 # CPU oracle legs
 # ----------------------------------------------------------------------------
 
-def oracle_sample(seed: int, full_samples: int, full_detected: int, t_stop: int = 4) -> dict:
-    """The oracle as it stands on increments t <= t_stop of the same workload,
-    scaled to a full solve by the sample counts (work per sample is the
-    lattice FFT work that dominates every increment)."""
+def oracle_sample(name: str, wl, outs) -> dict:
+    """The oracle as it stands on a bounded sample of the same workload, its
+    time scaled to the full job by the sample counts (the lattice FFT work per
+    sample dominates every increment):
+      plain_d10 / large_d25: increments t <= 4 / t <= 3 of the timed signal;
+      batch256: the three signals with the smallest d s (2N+1), complete."""
     from oracle import sfft as osfft
-    sig, p = W.workload(WORKLOAD, seed)
+    full_samples = sum(o.samples for o in outs)
+    full_detected = sum(o.freqs.shape[0] for o in outs)
     t0 = time.perf_counter()
-    res = osfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=seed,
-                     t_stop=t_stop)
+    if name == "batch256":
+        cost = [sig.d * p["s"] * (2 * sig.N + 1) for sig, p in wl.items]
+        pick = list(np.argsort(cost)[:3])
+        sample_samples = 0
+        for i in pick:
+            sig, p = wl.items[i]
+            res = osfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"],
+                             seed=wl.seeds[i])
+            sample_samples += res.samples
+        what = f"oracle on signals {pick} of batch256 (complete solves)"
+    else:
+        t_stop = 4 if name == "plain_d10" else 3
+        sig, p = wl.items[0]
+        res = osfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=wl.seeds[0],
+                         t_stop=t_stop)
+        sample_samples = res.samples
+        what = f"oracle increments t<={t_stop} of {name} seed {wl.seeds[0]}"
     dt = time.perf_counter() - t0
-    scaled = dt * full_samples / max(res.samples, 1)
+    scaled = dt * full_samples / max(sample_samples, 1)
     return {"value": full_detected / scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle increments t<={t_stop} of plain_d10 seed {seed} ({res.samples} of "
-                      f"{full_samples} samples, {dt:.1f} s, numpy single thread), time scaled by samples"}
+            "sample": f"{what}: {sample_samples} of {full_samples} samples in {dt:.1f} s (numpy, one "
+                      f"thread), time scaled by samples"}
 
 
 def run_reference(args):
@@ -213,17 +284,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     P.lib()
 
-    seed = args.seed + rank                      # independent signal per GPU (weak scaling)
-    sig, p = W.workload(WORKLOAD, seed)
-    freqs_d = torch.from_numpy(np.ascontiguousarray(sig.freqs, dtype=np.int32)).to(dev)
-    coeffs_d = torch.from_numpy(np.ascontiguousarray(sig.coeffs)).to(dev)
+    seed = args.seed + rank                      # independent signals per GPU (weak scaling)
+    wl = Workload(args.workload, seed, dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    truth = set(map(tuple, sig.freqs.astype(int).tolist()))
-
-    def solve(batch, host=False):
-        f, c = (sig.freqs, sig.coeffs) if host else (freqs_d, coeffs_d)
-        return P.sfft_dimincr(sig.d, sig.N, p["s"], p["r"], p["theta"], p["theta_mode"], seed=seed, b=p["b"],
-                              freqs=f, coeffs=c, sigma=sig.sigma, batch_reps=batch)
 
     def barrier():
         if world > 1:
@@ -232,9 +295,9 @@ def run_ours(args):
     def reduce(x, op):
         return reduce_scalar(x, op, world, dev)
 
-    def timed(batch, profile):
+    def timed(batched, profile):
         for _ in range(args.warmup):
-            solve(batch)
+            wl.solve(batched)
         barrier()
         torch.cuda.synchronize()
         if profile:
@@ -246,11 +309,11 @@ def run_ours(args):
             flush.fill_(1)                       # evict L2 between steps (not timed)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            last = solve(batch)
+            last = wl.solve(batched)
             e1.record()
             torch.cuda.synchronize()
             total_ms += e0.elapsed_time(e1)
-            detected += last.freqs.shape[0]
+            detected += sum(o.freqs.shape[0] for o in last)
         launches = P.prof_launches() - launches0
         barrier()
         torch.cuda.synchronize()
@@ -258,9 +321,8 @@ def run_ours(args):
         if profile:
             P.prof_enable(False)
             prof = P.prof_read()
-        max_ms = reduce(total_ms, "max")
-        all_det = reduce(float(detected), "sum")
-        return dict(ms=max_ms, detected=all_det, launches=launches, prof=prof, last=last)
+        return dict(ms=reduce(total_ms, "max"), detected=reduce(float(detected), "sum"), launches=launches,
+                    prof=prof, last=last)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -269,18 +331,17 @@ def run_ours(args):
     plain = timed(False, False)
 
     # end to end through the host-buffer API (inputs copied in, results copied out)
-    solve(True, host=True)
+    wl.solve(True, host=True)
     barrier()
     t0 = time.perf_counter()
-    det_e2e = 0
+    det_e2e, outs = 0, None
     for _ in range(args.steps):
-        out = solve(True, host=True)
-        det_e2e += out.freqs.shape[0]
-    e2e_s = time.perf_counter() - t0
-    e2e_s = reduce(e2e_s, "max")
+        outs = wl.solve(True, host=True)
+        det_e2e += sum(o.freqs.shape[0] for o in outs)
+    e2e_s = reduce(time.perf_counter() - t0, "max")
     det_e2e = reduce(float(det_e2e), "sum")
-    h2d = sig.freqs.size * 4 + sig.coeffs.size * 16
-    d2h = int(out.freqs.size * 4 + out.coeffs.size * 16)
+    h2d = sum(sig.freqs.size * 4 + sig.coeffs.size * 16 for sig, _ in wl.items)
+    d2h = int(sum(o.freqs.size * 4 + o.coeffs.size * 16 for o in outs))
 
     if rank != 0:
         return 0
@@ -299,7 +360,7 @@ def run_ours(args):
             tr = json.load(open(TRAFFIC_FILE))
             ent = tr.get("kernels", {}).get(dom_name)
             if ent and tr.get("src_hash") == _src_hash():
-                traffic = ent["bytes_per_launch_full"]
+                traffic = ent["dram_over_algorithmic"] * dom["bytes"] / dom["launches"]
         except (OSError, ValueError, KeyError):
             traffic = None
         if dom_name.startswith("blue_"):
@@ -319,9 +380,10 @@ def run_ours(args):
     recon = [k for k in prof if k.endswith("_recon") or k == "gather_kernel"]
     recon_ms = sum(prof[k]["ms"] for k in recon)
     alg_bytes = 0
-    for st in last.steps:
-        reps = p["r"] if st["t"] < sig.d else 1
-        alg_bytes += reps * (16 * st["sum_M"] + 24 * st["n_cand"])
+    for o, (sig, p) in zip(last, wl.items):
+        for st in o.steps:
+            reps = p["r"] if st["t"] < sig.d else 1
+            alg_bytes += reps * (16 * st["sum_M"] + 24 * st["n_cand"])
     alg_bytes *= args.steps
     hbm = peaks.get("hbm_gbs", 6800.0)
     lat_gbs = alg_bytes / (recon_ms * 1e-3) / 1e9 if recon_ms else None
@@ -330,19 +392,19 @@ def run_ours(args):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(seed, last.samples, last.freqs.shape[0])
+        cpu = oracle_sample(args.workload, wl, last)
 
-    got = set(map(tuple, last.freqs.tolist()))
+    form_b, form_p = FORMS[args.workload]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": bat["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(CONFIG, form="batched: the r repetitions of an increment fused in each launch",
-                       l2="256 MiB buffer written between timed steps", parallelism=f"{world} independent signals",
-                       seed=args.seed),
+        "config": {"workload": DESCRIPTIONS[args.workload], "form": form_b,
+                   "l2": "256 MiB buffer written between timed steps",
+                   "parallelism": f"{world} GPU(s), independent signals per GPU", "seed": args.seed},
         "plain": {"value": plain["detected"] / (plain["ms"] / 1e3), "ms_per_step": plain["ms"] / args.steps,
-                  "form": "one repetition per launch sequence"},
-        "batched_over_plain": (bat["ms"] and plain["ms"] / bat["ms"]),
+                  "form": form_p},
+        "batched_over_plain": plain["ms"] / bat["ms"] if bat["ms"] else None,
         "e2e": {"value": det_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(bat["launches"]),
@@ -354,7 +416,8 @@ def run_ours(args):
         "kernel_share": kernel_share,
         "clocks": clock_info,
         "cpu_baseline": cpu,
-        "detected": last.freqs.shape[0], "support_exact": got == truth, "samples": int(last.samples),
+        "detected": int(sum(o.freqs.shape[0] for o in last)), "support_exact": wl.exact(last),
+        "samples": int(sum(o.samples for o in last)),
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -391,6 +454,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIPTIONS),
+                    help="plain_d10 (default line), large_d25 or batch256")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the lattice transform at the workload size (for ncu captures)")
     args = ap.parse_args()

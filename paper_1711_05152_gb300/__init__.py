@@ -344,8 +344,9 @@ def _convert(res: sfft_result) -> SfftOutput:
 
 def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[SfftOutput]:
     """Algorithm 3 on many independent planted problems at once.  Each problem
-    is a dict with d, N, s, r, theta, theta_mode, seed, freqs, coeffs and
-    optionally sigma, s_local, b, noise_seed, batch_reps."""
+    is a dict with d, N, s, r, theta, theta_mode, seed, freqs, coeffs (host
+    arrays, or contiguous int32 / complex128 CUDA tensors) and optionally
+    sigma, s_local, b, noise_seed, batch_reps."""
     n = len(problems)
     params = (sfft_params * max(n, 1))()
     samps = (sfft_sampler * max(n, 1))()
@@ -356,6 +357,13 @@ def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[Sfft
                                 b=q.get("b", 10), theta=q["theta"],
                                 theta_mode=SFFT_THETA_REL if q.get("theta_mode", "rel") == "rel" else SFFT_THETA_ABS,
                                 seed=q["seed"], batch_reps=1 if q.get("batch_reps", True) else 0)
+        if getattr(q["freqs"], "is_cuda", False):
+            f, c = q["freqs"], q["coeffs"]
+            keep += [f, c]
+            samps[i] = sfft_sampler(SAMPLE_FN(), None, C.cast(C.c_void_p(f.data_ptr()), C.POINTER(C.c_int32)),
+                                    C.cast(C.c_void_p(c.data_ptr()), C.POINTER(C.c_double)), f.shape[0],
+                                    q.get("sigma", 0.0), q.get("noise_seed", q["seed"]), 1)
+            continue
         f = _i32(q["freqs"]).reshape(-1, d)
         c = np.ascontiguousarray(np.asarray(q["coeffs"], dtype=np.complex128)).view(np.float64)
         keep += [f, c]
