@@ -230,11 +230,10 @@ struct LatticeWork {
       maxM = std::max(maxM, Mh[l]);
       sumM += Mh[l];
     }
-    int logP = ilog2_pow2(2 * (int64_t)maxM - 1);
-    if (logP < 1) logP = 1;
-    MR1L_REQUIRE(logP <= 24, "lattice size too large for the Bluestein FFT (2 M - 1 > 2^24)");
+    const int P = blue_length(2 * (int64_t)maxM - 1);
+    MR1L_REQUIRE(P > 0, "lattice size too large for the Bluestein FFT (2 M - 1 > 2^24)");
     geom = BlueGeom{};
-    blue_split(geom, logP);
+    blue_split(geom, P);
     geom.L = Luse;
     geom.off = off.get();
     geom.M = M.get();
@@ -244,7 +243,7 @@ struct LatticeWork {
     geom.w = w.get();
     geom.ws = ws.get();
     geom.Bh = Bh.get();
-    geom.tw = twiddle_table(logP, s);
+    geom.tw = twiddle_table(P, s);
     geom.twn = small_twiddles(s);
     geom.sum_M = sumM;
     chirp_tables(geom, maxM, s);

@@ -92,6 +92,22 @@ struct RegDft<8, INV> {
   }
 };
 
+// Radix 3: X0 = a + b + c, X1,2 = a - (b + c)/2 -+ i (sqrt(3)/2)(b - c) (forward).
+template <bool INV>
+struct RegDft<3, INV> {
+  static __device__ __forceinline__ void run(cplx* v) {
+    const double s3 = 0.86602540378443864676;  // sqrt(3)/2
+    cplx t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+    cplx a = v[0];
+    v[0] = cadd(a, t1);
+    cplx m1 = cmake(fma(-0.5, t1.x, a.x), fma(-0.5, t1.y, a.y));
+    // forward: -i s3 t2 ; inverse: +i s3 t2
+    cplx m2 = INV ? cmake(-s3 * t2.y, s3 * t2.x) : cmake(s3 * t2.y, -s3 * t2.x);
+    v[1] = cadd(m1, m2);
+    v[2] = csub(m1, m2);
+  }
+};
+
 // Radix-8 DFT of a sequence whose inputs 4..7 are zero (the first stage of a
 // zero-padded Bluestein input): v[0..3] in, v[0..7] out, 36 FP64 operations
 // instead of 52.
@@ -129,17 +145,17 @@ __device__ __forceinline__ void reg_dft8_half(cplx* v) {
 
 // ---------------------------------------------------------------------------
 // One Stockham stage of radix R over nseq sequences of length n in shared
-// memory; element i of sequence b sits at s[b * bs + i * is].  Every thread
-// owns 8 values (8/R butterflies); blockDim.x * 8 == nseq * n (or more
-// threads than needed, which idle).
+// memory; element i of sequence b sits at s[b * bs + i * is].  The block has
+// nseq * n / 8 threads (or more, which idle); each thread runs up to
+// ceil(8 / R) butterflies of the stage.
 //   COLS: sequence index fastest across threads (column tiles, bs == 1)
 //   else: element index fastest (row tiles, is == 1)
-// ---------------------------------------------------------------------------
 // HALF (first radix-8 stage only): inputs r >= 4 are known zeros.
+// ---------------------------------------------------------------------------
 template <int R, bool INV, bool COLS, bool HALF = false>
-__device__ __forceinline__ void stockham_stage(cplx* s, int n, int lognb, int Ns, int nseq, int bs,
-                                               int is, const cplx* twn_n) {
-  constexpr int CNT = 8 / R;
+__device__ __forceinline__ void stockham_stage(cplx* s, int n, int Ns, int nseq, int bs, int is,
+                                               const cplx* twn_n) {
+  constexpr int CNT = (8 + R - 1) / R;
   const int nb = n / R;
   const int total = nseq * nb;
   cplx v[CNT][R];
@@ -154,10 +170,10 @@ __device__ __forceinline__ void stockham_stage(cplx* s, int n, int lognb, int Ns
       b = idx % nseq;
       j = idx / nseq;
     } else {
-      j = idx & (nb - 1);
-      b = idx >> lognb;
+      b = idx / nb;
+      j = idx - b * nb;
     }
-    int k = j & (Ns - 1);
+    int k = j % Ns;
     base[c] = b * bs + ((j - k) * R + k) * is;
     if (act[c] && HALF) {
       const cplx* src = s + b * bs + j * is;
@@ -190,26 +206,40 @@ __device__ __forceinline__ void stockham_stage(cplx* s, int n, int lognb, int Ns
   __syncthreads();
 }
 
-// Full in-smem FFT of length n = 2^logn (radix-8 stages, then one radix-4 or
-// radix-2 stage).  Natural order in and out.
-// HALF_FIRST: the upper half of every input sequence is zero (needs logn >= 3).
+// Twiddles exp(-2 pi i e / n) of a sub-FFT length n (2^a or 3 * 2^a).
+__device__ __forceinline__ const cplx* twiddles_of(const cplx* twn, int n) {
+  return (n & (n - 1)) == 0 ? twn + n : twn + 8192 + n - 3;
+}
+
+// Full in-smem FFT of length n = 2^a or 3 * 2^a: radix-8 stages, one radix-4
+// or radix-2 stage for the rest of 2^a, then radix 3.  Natural order in and
+// out.  HALF_FIRST: the upper half of every input sequence is zero (needs
+// 8 | n).
 template <bool INV, bool COLS, bool HALF_FIRST = false>
-__device__ __forceinline__ void smem_fft(cplx* s, int n, int logn, int nseq, int bs, int is,
-                                         const cplx* twn) {
-  const cplx* twn_n = twn + n;
-  int Ns = 1, rem = logn;
+__device__ __forceinline__ void smem_fft(cplx* s, int n, int nseq, int bs, int is, const cplx* twn) {
+  const cplx* twn_n = twiddles_of(twn, n);
+  const bool three = (n % 3) == 0;
+  int rem = 31 - __clz(three ? n / 3 : n);  // log2 of the power-of-two part
+  int Ns = 1;
   if (HALF_FIRST && rem >= 3) {
-    stockham_stage<8, INV, COLS, true>(s, n, logn - 3, Ns, nseq, bs, is, twn_n);
+    stockham_stage<8, INV, COLS, true>(s, n, Ns, nseq, bs, is, twn_n);
     Ns <<= 3;
     rem -= 3;
   }
   while (rem >= 3) {
-    stockham_stage<8, INV, COLS>(s, n, logn - 3, Ns, nseq, bs, is, twn_n);
+    stockham_stage<8, INV, COLS>(s, n, Ns, nseq, bs, is, twn_n);
     Ns <<= 3;
     rem -= 3;
   }
-  if (rem == 2) stockham_stage<4, INV, COLS>(s, n, logn - 2, Ns, nseq, bs, is, twn_n);
-  if (rem == 1) stockham_stage<2, INV, COLS>(s, n, logn - 1, Ns, nseq, bs, is, twn_n);
+  if (rem == 2) {
+    stockham_stage<4, INV, COLS>(s, n, Ns, nseq, bs, is, twn_n);
+    Ns <<= 2;
+  }
+  if (rem == 1) {
+    stockham_stage<2, INV, COLS>(s, n, Ns, nseq, bs, is, twn_n);
+    Ns <<= 1;
+  }
+  if (three) stockham_stage<3, INV, COLS>(s, n, Ns, nseq, bs, is, twn_n);
 }
 
 // ---------------------------------------------------------------------------
@@ -268,14 +298,14 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
   const int64_t off = g.off[l];
   // zero padding: for RECON / EVAL the input vanishes from M <= P/2 on, so the
   // upper half is never loaded and the first radix-8 stage skips it
-  const bool half = MODE != kModeFilter && g.logP >= 3;
+  const bool half = MODE != kModeFilter && (P % 8) == 0;
   const int nload = half ? P / 2 : P;
   for (int n = threadIdx.x; n < nload; n += blockDim.x) sm[n] = load_input<MODE>(g, io, l, h, M, off, n);
   __syncthreads();
   if (half)
-    smem_fft<false, false, true>(sm, P, g.logP, 1, 0, 1, g.twn);
+    smem_fft<false, false, true>(sm, P, 1, 0, 1, g.twn);
   else
-    smem_fft<false, false>(sm, P, g.logP, 1, 0, 1, g.twn);
+    smem_fft<false, false>(sm, P, 1, 0, 1, g.twn);
   cplx* Bh = g.Bh + (int64_t)l * P;
   if (MODE == kModeFilter) {
     const double sc = 1.0 / (double)P;  // exact: P is a power of two
@@ -284,7 +314,7 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
   }
   for (int n = threadIdx.x; n < P; n += blockDim.x) sm[n] = cmul(sm[n], Bh[n]);
   __syncthreads();
-  smem_fft<true, false>(sm, P, g.logP, 1, 0, 1, g.twn);
+  smem_fft<true, false>(sm, P, 1, 0, 1, g.twn);
   for (int n = threadIdx.x; n < M; n += blockDim.x) store_output<MODE>(g, io, l, h, off, n, sm[n]);
 }
 
@@ -296,8 +326,12 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
 // column or row of 4096 takes a 4096-element tile.
 constexpr int kTileElems = 2048;
 __host__ __device__ __forceinline__ int col_tile(int P1) {
-  int cb = kTileElems / P1;
-  return cb > 16 ? 16 : (cb < 1 ? 1 : cb);
+  int cb = kTileElems / P1;  // P1 = 3 * 2^a gives a tile of 3/4 x 2048
+  if (cb > 16) cb = 16;
+  if (cb < 1) cb = 1;
+  int p = 1;  // power of two, so it divides P2
+  while (2 * p <= cb) p *= 2;
+  return p;
 }
 __host__ __device__ __forceinline__ int row_tile(int P2) {
   int rb = kTileElems / P2;
@@ -311,7 +345,6 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
   const int gi = blockIdx.y;
   const int l = gi % g.L, h = gi / g.L;
   const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1);
-  const int logP1 = g.logP - ilog2_pow2(P2);
   const int M = g.M[l];
   const int64_t off = g.off[l];
   const int n2_0 = blockIdx.x * CB;
@@ -323,14 +356,14 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
   }
   __syncthreads();
   if (MODE == kModeFilter)
-    smem_fft<false, true>(sm, P1, logP1, CB, 1, CB, g.twn);
+    smem_fft<false, true>(sm, P1, CB, 1, CB, g.twn);
   else
-    smem_fft<false, true, true>(sm, P1, logP1, CB, 1, CB, g.twn);
+    smem_fft<false, true, true>(sm, P1, CB, 1, CB, g.twn);
   cplx* work = io.work + (int64_t)gi * P;
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int k1 = e / CB, b = e - k1 * CB;
     int n2 = n2_0 + b;
-    cplx w = g.tw[((int64_t)n2 * k1) & (P - 1)];
+    cplx w = g.tw[((int64_t)n2 * k1) % P];
     work[(int64_t)k1 * P2 + n2] = cmul(sm[e], w);
   }
 }
@@ -343,12 +376,11 @@ __global__ void __launch_bounds__(512) blue_row_kernel(BlueGeom g, BlueIO io) {
   const int gi = blockIdx.y;
   const int l = gi % g.L;
   const int P = g.P, P2 = g.P2, RB = row_tile(P2);
-  const int logP2 = ilog2_pow2(P2);
   const int k1_0 = blockIdx.x * RB;
   cplx* work = io.work + (int64_t)gi * P + (int64_t)k1_0 * P2;
   for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = work[e];
   __syncthreads();
-  smem_fft<false, false>(sm, P2, logP2, RB, P2, 1, g.twn);
+  smem_fft<false, false>(sm, P2, RB, P2, 1, g.twn);
   cplx* Bh = g.Bh + (int64_t)l * P + (int64_t)k1_0 * P2;
   if (FILTER) {
     const double sc = 1.0 / (double)P;
@@ -357,11 +389,11 @@ __global__ void __launch_bounds__(512) blue_row_kernel(BlueGeom g, BlueIO io) {
   }
   for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = cmul(sm[e], Bh[e]);
   __syncthreads();
-  smem_fft<true, false>(sm, P2, logP2, RB, P2, 1, g.twn);
+  smem_fft<true, false>(sm, P2, RB, P2, 1, g.twn);
   for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) {
     int b = e / P2, n2 = e - b * P2;
     int k1 = k1_0 + b;
-    cplx w = g.tw[((int64_t)n2 * k1) & (P - 1)];
+    cplx w = g.tw[((int64_t)n2 * k1) % P];
     work[e] = cmulc(sm[e], w);
   }
 }
@@ -373,7 +405,6 @@ __global__ void __launch_bounds__(512) blue_col_inv_kernel(BlueGeom g, BlueIO io
   const int gi = blockIdx.y;
   const int l = gi % g.L, h = gi / g.L;
   const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1);
-  const int logP1 = g.logP - ilog2_pow2(P2);
   const int M = g.M[l];
   const int64_t off = g.off[l];
   const int n2_0 = blockIdx.x * CB;
@@ -383,7 +414,7 @@ __global__ void __launch_bounds__(512) blue_col_inv_kernel(BlueGeom g, BlueIO io
     sm[e] = work[(int64_t)k1 * P2 + n2_0 + b];
   }
   __syncthreads();
-  smem_fft<true, true>(sm, P1, logP1, CB, 1, CB, g.twn);
+  smem_fft<true, true>(sm, P1, CB, 1, CB, g.twn);
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int n1 = e / CB, b = e - n1 * CB;
     int64_t n = (int64_t)n1 * P2 + n2_0 + b;
@@ -403,13 +434,21 @@ __global__ void twiddle_kernel(cplx* tw, int64_t P) {
 }
 
 __global__ void small_twiddle_kernel(cplx* tw) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;  // [0, 8192)
-  if (i < 2 || i >= 8192) return;
-  int n = 1 << (31 - __clz(i));  // table of size n sits at [n, 2n)
-  int e = i - n;
-  double s, c;
-  sincospi(2.0 * (double)e / (double)n, &s, &c);
-  tw[i] = cmake(c, -s);
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 2 || i >= kSmallTw) return;
+  int n, e;
+  if (i < 8192) {  // n = 2^a at [n, 2n)
+    n = 1 << (31 - __clz(i));
+    e = i - n;
+  } else {         // n = 3 * 2^a at [8192 + n - 3, 8192 + 2n - 3)
+    int j = i - 8192 + 3;              // in [n, 2n) for n = 3 * 2^a
+    int a = 31 - __clz(j / 3);
+    n = 3 << a;
+    e = j - n;
+  }
+  double sn, cs;
+  sincospi(2.0 * (double)e / (double)n, &sn, &cs);
+  tw[i] = cmake(cs, -sn);
 }
 
 __global__ void chirp_kernel(cplx* w, cplx* ws, const int64_t* off, const int* Ms, int L) {
@@ -428,18 +467,18 @@ __global__ void chirp_kernel(cplx* w, cplx* ws, const int64_t* off, const int* M
 
 namespace {
 std::mutex g_tw_mu;
-std::map<std::pair<int, int>, cplx*> g_tw;  // (device, logP) -> table
+std::map<std::pair<int, int>, cplx*> g_tw;  // (device, P) -> table
 std::map<int, cplx*> g_twn;                 // device -> small tables
 }  // namespace
 
-const cplx* twiddle_table(int logP, cudaStream_t s) {
+const cplx* twiddle_table(int Pn, cudaStream_t s) {
   int dev = 0;
   MR1L_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(g_tw_mu);
-  auto key = std::make_pair(dev, logP);
+  auto key = std::make_pair(dev, Pn);
   auto it = g_tw.find(key);
   if (it != g_tw.end()) return it->second;
-  int64_t P = int64_t(1) << logP;
+  int64_t P = Pn;
   cplx* p = nullptr;
   MR1L_CUDA(cudaMalloc(&p, P * sizeof(cplx)));
   MR1L_LAUNCH("twiddle_kernel", s, 0, 16.0 * P, twiddle_kernel<<<cdiv(P, 256), 256, 0, s>>>(p, P));
@@ -455,26 +494,41 @@ const cplx* small_twiddles(cudaStream_t s) {
   auto it = g_twn.find(dev);
   if (it != g_twn.end()) return it->second;
   cplx* p = nullptr;
-  MR1L_CUDA(cudaMalloc(&p, 8192 * sizeof(cplx)));
-  MR1L_CUDA(cudaMemsetAsync(p, 0, 8192 * sizeof(cplx), s));
-  MR1L_LAUNCH("small_twiddle_kernel", s, 0, 16.0 * 8192, small_twiddle_kernel<<<32, 256, 0, s>>>(p));
+  MR1L_CUDA(cudaMalloc(&p, kSmallTw * sizeof(cplx)));
+  MR1L_CUDA(cudaMemsetAsync(p, 0, kSmallTw * sizeof(cplx), s));
+  MR1L_LAUNCH("small_twiddle_kernel", s, 0, 16.0 * kSmallTw,
+              small_twiddle_kernel<<<cdiv(kSmallTw, 256), 256, 0, s>>>(p));
   MR1L_CUDA(cudaStreamSynchronize(s));
   g_twn[dev] = p;
   return p;
 }
 
-void blue_split(BlueGeom& g, int logP) {
-  MR1L_REQUIRE(logP >= 1 && logP <= 24, "Bluestein length out of range (2 .. 2^24)");
-  g.logP = logP;
-  g.P = 1 << logP;
-  if (logP <= kSmallLog) {
+int blue_length(int64_t n) {
+  int64_t p2 = 1;
+  while (p2 < n) p2 <<= 1;
+  int64_t p3 = 3;
+  while (p3 < n) p3 <<= 1;
+  if (p2 < 4) p2 = 4;
+  int64_t best = 0;
+  if (p2 <= (int64_t(1) << 24)) best = p2;
+  if (p3 <= 3 * (int64_t(1) << 22) && (best == 0 || p3 < best)) best = p3;
+  return (int)best;
+}
+
+void blue_split(BlueGeom& g, int P) {
+  MR1L_REQUIRE(P >= 3 && P == blue_length(P), "unsupported Bluestein length");
+  g.P = P;
+  if (P <= kSmallMax) {
     g.P1 = 1;
-    g.P2 = g.P;
-  } else {
-    int l1 = logP / 2;
-    g.P1 = 1 << l1;
-    g.P2 = 1 << (logP - l1);
+    g.P2 = P;
+    return;
   }
+  // P2 = 2^b, P1 = P / P2 (2^a or 3 * 2^a), P1 about P2
+  const bool three = P % 3 == 0;
+  int k = 31 - __builtin_clz((unsigned)(three ? P / 3 : P));
+  int b = three ? (k + 2) / 2 : k - k / 2;
+  g.P2 = 1 << b;
+  g.P1 = P / g.P2;
 }
 
 void chirp_tables(const BlueGeom& g, int64_t max_M, cudaStream_t s) {
@@ -502,7 +556,7 @@ template <int MODE>
 static void launch_first_last(const BlueGeom& g, const BlueIO& io, int ntrans, cudaStream_t s) {
   const double P = g.P, nr = (double)ntrans / g.L, sumM = (double)g.sum_M;
   const double cb = sizeof(cplx);
-  if (g.logP <= kSmallLog) {
+  if (g.P <= kSmallMax) {
     size_t smem = (size_t)g.P * sizeof(cplx);
     set_smem(blue_small_kernel<MODE>, smem);
     double fl = ntrans * (MODE == kModeFilter ? fft_flops(P) : 2 * fft_flops(P) + 6 * P) + nr * 6 * sumM;

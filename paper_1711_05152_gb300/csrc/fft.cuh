@@ -16,15 +16,16 @@ enum BlueMode : int {
 // Per-transform geometry shared by every pass of one batched launch.
 struct BlueGeom {
   int L;            // lattices (transform g has lattice g % L, right-hand side g / L)
-  int P, logP;      // power-of-two convolution length, P >= 2 max M - 1
-  int P1, P2;       // 4-step split (P1 * P2 == P) when logP > kSmallLog
+  int P;            // convolution length 2^k or 3 * 2^k, P >= 2 max M - 1
+  int P1, P2;       // 4-step split P = P1 * P2 (P1 = 2^a or 3 * 2^a, P2 = 2^b) when P > kSmallMax
   const int64_t* off;   // device [L]: offset of lattice l in per-lattice arrays
   const int* M;         // device [L]: lattice sizes
   const cplx* w;        // device [sum M]: chirp exp(-pi i n^2 / M)
   const cplx* ws;       // device [sum M]: chirp / M
   cplx* Bh;             // device [L][P]: filter spectrum FFT_P(b) / P (pass order)
   const cplx* tw;       // device [P]: exp(-2 pi i e / P)
-  const cplx* twn;      // device [8192]: exp(-2 pi i e / n) for n = 2..4096 at offset n
+  const cplx* twn;      // device [kSmallTw]: exp(-2 pi i e / n), n = 2^a <= 4096 at offset n,
+                        //   n = 3 * 2^a <= 6144 at offset 8192 + n - 3
   int64_t sum_M;        // host: sum of the L lattice sizes (for launch accounting)
 };
 
@@ -41,14 +42,19 @@ struct BlueIO {
   int noise_rep_per_rhs;  // rep index = noise_rep + rhs * noise_rep_per_rhs
 };
 
-constexpr int kSmallLog = 12;   // P <= 4096: one CTA holds the whole transform
+constexpr int kSmallMax = 4096;  // P <= 4096: one CTA holds the whole transform
+constexpr int kSmallTw = 8192 + 12288;
 
 // Device-resident twiddle tables, cached per (device, P).
-const cplx* twiddle_table(int logP, cudaStream_t s);
+const cplx* twiddle_table(int P, cudaStream_t s);
 const cplx* small_twiddles(cudaStream_t s);
 
+// The smallest supported convolution length P >= n (2^k <= 2^24 or 3 * 2^k <= 3 * 2^22);
+// 0 if there is none.
+int blue_length(int64_t n);
+
 // Fill geometry split for a given P.
-void blue_split(BlueGeom& g, int logP);
+void blue_split(BlueGeom& g, int P);
 
 // Build the filter spectra Bh for all L lattices (needs w).
 void blue_filter(const BlueGeom& g, cudaStream_t s);

@@ -117,10 +117,11 @@ def test_given_lattice_plan_and_uncovered():
     assert e.value.code == P.MR1L_E_NOT_RECONSTRUCTING
 
 
-def test_large_single_lattice_4step():
-    """One lattice with M ~ 1.3e6 (P = 2^22, the largest 4-step split used at
-    the paper's d = 25 sizes) against numpy's FFT."""
-    M = 1_300_021
+@pytest.mark.parametrize("M", [1_300_021, 2_000_003, 3_000_017, 8_000_009])
+def test_large_single_lattice_4step(M):
+    """One lattice per case, chosen so that the Bluestein length is 3 * 2^20,
+    2^22, 3 * 2^21 (one-column tiles) and 2^24 (the largest), against numpy's
+    FFT."""
     assert lattice.is_prime(M)
     I = np.arange(-30000, 30000).reshape(-1, 1)
     pl = P.plan(I, [M], [[7919]])
@@ -130,6 +131,9 @@ def test_large_single_lattice_4step():
     ml = lattice.MultiLattice([M], [np.array([7919])], [lattice.unique_mask(I, [7919], M)], True, 1)
     want, _ = lattice.reconstruct(I, ml, [y], "fft")
     assert _normwise(got, want) < RTOL
+    yb = pl.evaluate(torch.from_numpy(want).cuda(), P.MR1L_ADJOINT).cpu().numpy()
+    wantb = np.concatenate(lattice.evaluate(I, ml, want, "adjoint", "fft"))
+    assert _normwise(yb[0] if yb.ndim > 1 else yb, wantb) < RTOL
 
 
 def _sfft_pair(name, seed, batch=False):
