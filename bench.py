@@ -76,25 +76,25 @@ class Workload:
         self.dev_arrays = [(torch.from_numpy(np.ascontiguousarray(sig.freqs, dtype=np.int32)).to(dev),
                             torch.from_numpy(np.ascontiguousarray(sig.coeffs)).to(dev)) for sig, _ in self.items]
 
-    def problems(self, host: bool, batched: bool):
+    def problems(self, host: bool, batched: bool, fft: str = "f64"):
         out = []
         for (sig, p), sd, (fd, cd) in zip(self.items, self.seeds, self.dev_arrays):
             out.append(dict(d=sig.d, N=sig.N, s=p["s"], s_local=p["s_local"], r=p["r"], b=p["b"],
                             theta=p["theta"], theta_mode=p["theta_mode"], seed=sd,
                             freqs=sig.freqs if host else fd, coeffs=sig.coeffs if host else cd,
-                            sigma=sig.sigma, batch_reps=batched))
+                            sigma=sig.sigma, batch_reps=batched, fft=fft))
         return out
 
-    def solve(self, batched: bool, host: bool = False):
+    def solve(self, batched: bool, host: bool = False, fft: str = "f64"):
         import paper_1711_05152_gb300 as P
-        probs = self.problems(host, batched)
+        probs = self.problems(host, batched, fft)
         if self.name == "batch256" and batched:
             return P.sfft_dimincr_batch(probs, concurrency=16)
         outs = []
         for q in probs:
             outs.append(P.sfft_dimincr(q["d"], q["N"], q["s"], q["r"], q["theta"], q["theta_mode"], seed=q["seed"],
                                        s_local=q["s_local"], b=q["b"], freqs=q["freqs"], coeffs=q["coeffs"],
-                                       sigma=q["sigma"], batch_reps=batched))
+                                       sigma=q["sigma"], batch_reps=batched, fft=fft))
         return outs
 
     def exact(self, outs) -> bool:
@@ -295,9 +295,9 @@ def run_ours(args):
     def reduce(x, op):
         return reduce_scalar(x, op, world, dev)
 
-    def timed(batched, profile):
+    def timed(batched, profile, fft="f64"):
         for _ in range(args.warmup):
-            wl.solve(batched)
+            wl.solve(batched, fft=fft)
         barrier()
         torch.cuda.synchronize()
         if profile:
@@ -309,7 +309,7 @@ def run_ours(args):
             flush.fill_(1)                       # evict L2 between steps (not timed)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            last = wl.solve(batched)
+            last = wl.solve(batched, fft=fft)
             e1.record()
             torch.cuda.synchronize()
             total_ms += e0.elapsed_time(e1)
@@ -329,6 +329,7 @@ def run_ours(args):
     bat = timed(True, True)
     clock_info = clocks.stop()
     plain = timed(False, False)
+    fast = None if args.no_fast_fft else timed(True, False, fft="df")
 
     # end to end through the host-buffer API (inputs copied in, results copied out)
     wl.solve(True, host=True)
@@ -405,6 +406,13 @@ def run_ours(args):
         "plain": {"value": plain["detected"] / (plain["ms"] / 1e3), "ms_per_step": plain["ms"] / args.steps,
                   "form": form_p},
         "batched_over_plain": plain["ms"] / bat["ms"] if bat["ms"] else None,
+        "fast_fft": None if fast is None else {
+            "value": fast["detected"] / (fast["ms"] / 1e3), "ms_per_step": fast["ms"] / args.steps,
+            "form": "batched, Bluestein butterflies in double-float (FP32 pairs) instead of FP64",
+            "same_support_as_f64": all(np.array_equal(a.freqs, b.freqs) for a, b in zip(fast["last"], last)),
+            "max_rel_coeff_diff_vs_f64": max((float(np.max(np.abs(a.coeffs - b.coeffs) / np.abs(b.coeffs)))
+                                             for a, b in zip(fast["last"], last) if b.coeffs.size and
+                                             np.array_equal(a.freqs, b.freqs)), default=None)},
         "e2e": {"value": det_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(bat["launches"]),
@@ -435,13 +443,13 @@ def run_kernel_case(args):
     rng = np.random.default_rng(args.seed)
     pre = np.unique(rng.integers(-32, 33, size=(1100, 9)), axis=0)[:1000]
     J = np.concatenate([np.repeat(pre, 65, axis=0), np.tile(np.arange(-32, 33), 1000)[:, None]], axis=1)
-    pl = P.plan_search(J, seed=args.seed)
+    pl = P.plan_search(J, seed=args.seed, fft=args.fft)
     y = torch.from_numpy(W.complex_normal(rng, (5, pl.sum_M))).cuda()
     for _ in range(2):
         c = pl.reconstruct(y)
         pl.evaluate(c, P.MR1L_ADJOINT)
     torch.cuda.synchronize()
-    print(json.dumps({"kernel_case": "reconstruct+adjoint", "n": int(J.shape[0]), "L": pl.L,
+    print(json.dumps({"kernel_case": "reconstruct+adjoint", "fft": args.fft, "n": int(J.shape[0]), "L": pl.L,
                       "sum_M": int(pl.sum_M), "M0": int(pl.M[0])}))
     return 0
 
@@ -456,6 +464,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIPTIONS),
                     help="plain_d10 (default line), large_d25 or batch256")
+    ap.add_argument("--no-fast-fft", action="store_true", help="skip the double-float FFT form")
+    ap.add_argument("--fft", default="f64", choices=["f64", "df"], help="arithmetic of --kernel-case")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the lattice transform at the workload size (for ncu captures)")
     args = ap.parse_args()

@@ -55,6 +55,11 @@ extern "C" {
 
 /* plan flags */
 #define MR1L_STRICT 1           /* fail with E_NOT_RECONSTRUCTING unless condition (2.1) holds */
+#define MR1L_FFT_DF 2           /* Bluestein FFT butterflies in double-float arithmetic (pairs of
+                                   FP32 numbers, about 48 significant bits, error-free
+                                   transformations) on the FP32 pipes instead of FP64; inputs,
+                                   outputs, chirps, the gather and all decisions stay FP64.
+                                   Requires |values| between about 1e-30 and 1e30. */
 
 /* evaluation modes */
 #define MR1L_EVAL 0
@@ -219,6 +224,7 @@ typedef struct sfft_params {
     int theta_mode;         /* SFFT_THETA_ABS or SFFT_THETA_REL */
     uint64_t seed;          /* Philox key of anchors and generating vectors */
     int batch_reps;         /* 0: one repetition per launch sequence; 1: all r~ fused */
+    int fft_arith;          /* 0: FP64 Bluestein FFTs; 1: double-float (see MR1L_FFT_DF) */
     int t_stop;             /* 0: all d increments; 2 <= t_stop < d: stop after increment t_stop
                                and return the projected set I^(1..t_stop) (rows of t_stop
                                components, coefficients zero) - a bounded prefix of the run */
@@ -276,6 +282,16 @@ void sfft_free(sfft_result* res);
  */
 int sfft_dimincr_batch(const sfft_params* params, const sfft_sampler* samplers, int count, int concurrency,
                        sfft_result** out, int* status);
+
+/*
+ * mr1l_lattice_noise - the measurement noise of the built-in planted sampler
+ * (Section 5.2): y[off_l + j] = sigma/sqrt(2) (g1 + i g2) for every lattice l
+ * (sizes M, host int64 [L]) and node j, by Box-Muller on the Philox4x32-10
+ * words with key = seed and counter (j, l or 0 for node 0, rep, 5 << 24 | t).
+ * y: device complex [sum M].  Synchronises the stream.
+ */
+int mr1l_lattice_noise(uint64_t seed, int t, int rep, int L, const int64_t* M, double sigma, void* y,
+                       void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Launch accounting and kernel timing                                       */

@@ -30,6 +30,7 @@ MR1L_E_NOT_RECONSTRUCTING = 4
 MR1L_E_SAMPLER = 5
 MR1L_E_TIMEOUT = 6
 MR1L_STRICT = 1
+MR1L_FFT_DF = 2
 MR1L_EVAL = 0
 MR1L_ADJOINT = 1
 SFFT_THETA_ABS = 0
@@ -41,7 +42,7 @@ SFFT_MAX_STEPS = 256
 EXPORTS = [
     "mr1l_last_error", "mr1l_version", "mr1l_plan", "mr1l_plan_search", "mr1l_plan_info",
     "mr1l_plan_masks", "mr1l_destroy", "mr1l_reconstruct", "mr1l_evaluate", "sfft_dimincr",
-    "sfft_free", "sfft_dimincr_batch", "mr1l_reconstruct_noalloc", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
+    "sfft_free", "sfft_dimincr_batch", "mr1l_reconstruct_noalloc", "mr1l_lattice_noise", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
 ]
 
 
@@ -69,7 +70,7 @@ class sfft_sampler(C.Structure):
 class sfft_params(C.Structure):
     _fields_ = [("d", C.c_int), ("N", C.c_int), ("s", C.c_int64), ("s_local", C.c_int64),
                 ("r", C.c_int), ("b", C.c_int), ("theta", C.c_double), ("theta_mode", C.c_int),
-                ("seed", C.c_uint64), ("batch_reps", C.c_int), ("t_stop", C.c_int)]
+                ("seed", C.c_uint64), ("batch_reps", C.c_int), ("fft_arith", C.c_int), ("t_stop", C.c_int)]
 
 
 class sfft_step_stats(C.Structure):
@@ -112,6 +113,7 @@ def lib() -> C.CDLL:
     L.mr1l_reconstruct.argtypes = [vp, vp, C.c_int, vp, vp]
     L.mr1l_evaluate.argtypes = [vp, vp, C.c_int, vp, C.c_int, vp]
     L.mr1l_reconstruct_noalloc.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.mr1l_lattice_noise.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, i64p, C.c_double, vp, vp]
     L.sfft_dimincr.argtypes = [C.POINTER(sfft_params), C.POINTER(sfft_sampler), vp,
                                C.POINTER(C.POINTER(sfft_result))]
     L.sfft_free.argtypes = [C.POINTER(sfft_result)]
@@ -245,8 +247,15 @@ class Plan:
             pass
 
 
-def plan(I, M, z, strict: bool = False, stream=None) -> Plan:
-    """Plan on given lattices (sizes M [L], generating vectors z [L, t])."""
+def _flags(strict: bool, fft: str) -> int:
+    if fft not in ("f64", "df"):
+        raise ValueError('fft must be "f64" or "df"')
+    return (MR1L_STRICT if strict else 0) | (MR1L_FFT_DF if fft == "df" else 0)
+
+
+def plan(I, M, z, strict: bool = False, fft: str = "f64", stream=None) -> Plan:
+    """Plan on given lattices (sizes M [L], generating vectors z [L, t]).
+    fft="df" runs the Bluestein butterflies in double-float arithmetic."""
     I = _i32(I)
     if I.ndim == 1:
         I = I.reshape(-1, 1)
@@ -255,19 +264,19 @@ def plan(I, M, z, strict: bool = False, stream=None) -> Plan:
     z = _i64(z).reshape(M.shape[0], t)
     h = C.c_void_p()
     _check(lib().mr1l_plan(_ptr(I, C.c_int32), n, t, M.shape[0], _ptr(M, C.c_int64), _ptr(z, C.c_int64),
-                           MR1L_STRICT if strict else 0, C.c_void_p(_stream(stream)), C.byref(h)))
+                           _flags(strict, fft), C.c_void_p(_stream(stream)), C.byref(h)))
     return Plan(h.value, n, t)
 
 
 def plan_search(I, seed: int, c: float = 2.0, gamma: float = 0.5, b: int = 10, strict: bool = False,
-                stream=None) -> Plan:
+                fft: str = "f64", stream=None) -> Plan:
     """Plan on a lattice built by Algorithm 1 (up to b searches)."""
     I = _i32(I)
     if I.ndim == 1:
         I = I.reshape(-1, 1)
     n, t = I.shape
     h = C.c_void_p()
-    _check(lib().mr1l_plan_search(_ptr(I, C.c_int32), n, t, c, gamma, b, seed, MR1L_STRICT if strict else 0,
+    _check(lib().mr1l_plan_search(_ptr(I, C.c_int32), n, t, c, gamma, b, seed, _flags(strict, fft),
                                   C.c_void_p(_stream(stream)), C.byref(h)))
     return Plan(h.value, n, t)
 
@@ -285,13 +294,13 @@ class SfftOutput:
 def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str = "rel", seed: int = 0,
                  s_local: int | None = None, b: int = 10, freqs=None, coeffs=None, sigma: float = 0.0,
                  noise_seed: int | None = None, sampler=None, batch_reps: bool = False,
-                 t_stop: int | None = None, stream=None) -> SfftOutput:
+                 t_stop: int | None = None, fft: str = "f64", stream=None) -> SfftOutput:
     """Algorithm 3.  Either a planted polynomial (freqs [s, d], coeffs [s],
     sigma) evaluated by the library, or ``sampler(req, y_ptr, stream_ptr)``,
     a Python callable that fills the device buffer y_ptr for a request."""
     p = sfft_params(d=d, N=N, s=s, s_local=s if s_local is None else s_local, r=r, b=b, theta=theta,
                     theta_mode=SFFT_THETA_REL if theta_mode == "rel" else SFFT_THETA_ABS, seed=seed,
-                    batch_reps=1 if batch_reps else 0, t_stop=t_stop or 0)
+                    batch_reps=1 if batch_reps else 0, fft_arith=1 if fft == "df" else 0, t_stop=t_stop or 0)
     keep = []
     nseed = seed if noise_seed is None else noise_seed
     if sampler is None and getattr(freqs, "is_cuda", False):
@@ -356,7 +365,8 @@ def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[Sfft
         params[i] = sfft_params(d=d, N=q["N"], s=q["s"], s_local=q.get("s_local", q["s"]), r=q["r"],
                                 b=q.get("b", 10), theta=q["theta"],
                                 theta_mode=SFFT_THETA_REL if q.get("theta_mode", "rel") == "rel" else SFFT_THETA_ABS,
-                                seed=q["seed"], batch_reps=1 if q.get("batch_reps", True) else 0)
+                                seed=q["seed"], batch_reps=1 if q.get("batch_reps", True) else 0,
+                                fft_arith=1 if q.get("fft", "f64") == "df" else 0)
         if getattr(q["freqs"], "is_cuda", False):
             f, c = q["freqs"], q["coeffs"]
             keep += [f, c]
@@ -379,6 +389,16 @@ def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[Sfft
         for i in range(n):
             if outs[i]:
                 lib().sfft_free(outs[i])
+
+def lattice_noise(seed: int, t: int, rep: int, M, sigma: float, stream=None):
+    """The planted sampler's noise for lattice sizes M (complex128 CUDA tensor [sum M])."""
+    import torch
+    M = _i64(M).reshape(-1)
+    y = torch.empty(int(M.sum()), dtype=torch.complex128, device="cuda")
+    _check(lib().mr1l_lattice_noise(seed, t, rep, M.shape[0], _ptr(M, C.c_int64), sigma,
+                                    C.c_void_p(y.data_ptr()), C.c_void_p(_stream(stream))))
+    return y
+
 
 def prof_enable(on: bool = True) -> None:
     """Bracket every library kernel launch with CUDA events (see mr1l_prof_read)."""

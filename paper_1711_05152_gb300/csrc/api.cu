@@ -169,6 +169,8 @@ struct LatticeWork {
   DevBuf<uint64_t> umask;
   DevBuf<int> cover;
   DevBuf<cplx> w, ws, Bh;
+  DevBuf<float4> w_df, ws_df;
+  int df = 0;  // Bluestein butterflies in double-float arithmetic
   BlueGeom geom{};
   LatticeDev dev() {
     LatticeDev d;
@@ -246,7 +248,18 @@ struct LatticeWork {
     geom.tw = twiddle_table(P, s);
     geom.twn = small_twiddles(s);
     geom.sum_M = sumM;
+    geom.df = df;
     chirp_tables(geom, maxM, s);
+    if (df) {
+      w_df.reserve(std::max<int64_t>(sumM, 1));
+      ws_df.reserve(std::max<int64_t>(sumM, 1));
+      to_double_float(w.get(), w_df.get(), sumM, s);
+      to_double_float(ws.get(), ws_df.get(), sumM, s);
+      geom.w_df = w_df.get();
+      geom.ws_df = ws_df.get();
+      geom.tw_df = twiddle_table_df(P, s);
+      geom.twn_df = small_twiddles_df(s);
+    }
     blue_filter(geom, s);
   }
 };
@@ -339,6 +352,7 @@ extern "C" int mr1l_plan(const int32_t* I, int64_t nI, int t, int L, const int64
     p->flags = flags;
     p->attempts = 1;
     p->I.reserve(nI * t);
+    p->lw.df = (flags & MR1L_FFT_DF) ? 1 : 0;
     MR1L_CUDA(cudaMemcpyAsync(p->I.get(), I, nI * t * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     p->lw.load(p->cand(), Ms, zs, t, s);
     if ((flags & MR1L_STRICT) && p->lw.n_uncovered)
@@ -361,6 +375,7 @@ extern "C" int mr1l_plan_search(const int32_t* I, int64_t nI, int t, double c, d
     p->nI = nI;
     p->t = t;
     p->flags = flags;
+    p->lw.df = (flags & MR1L_FFT_DF) ? 1 : 0;
     p->I.reserve(nI * t);
     MR1L_CUDA(cudaMemcpyAsync(p->I.get(), I, nI * t * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     int Lmax;
@@ -631,6 +646,7 @@ struct SfftRun {
     auto t0 = std::chrono::steady_clock::now();
     const int d = P.d;
     K = 2 * P.N + 1;
+    lw.df = P.fft_arith ? 1 : 0;
     theta2 = P.theta * P.theta;
     rel = P.theta_mode == SFFT_THETA_REL;
     if (!S.fn && !S.device_arrays) {
@@ -770,6 +786,7 @@ static void validate_sfft(const sfft_params* params, const sfft_sampler* sampler
   MR1L_REQUIRE(P.theta >= 0.0 && std::isfinite(P.theta), "theta must be finite and >= 0");
   MR1L_REQUIRE(P.theta_mode == SFFT_THETA_ABS || P.theta_mode == SFFT_THETA_REL, "bad theta_mode");
   MR1L_REQUIRE(P.t_stop == 0 || (P.t_stop >= 2 && P.t_stop <= P.d), "t_stop must be 0 or in [2, d]");
+  MR1L_REQUIRE(P.fft_arith == 0 || P.fft_arith == 1, "fft_arith must be 0 (FP64) or 1 (double-float)");
   if (!sampler->fn) {
     MR1L_REQUIRE(sampler->s >= 0, "planted s must be >= 0");
     MR1L_REQUIRE(sampler->s == 0 || (sampler->freqs && sampler->coeffs), "planted arrays are null");
@@ -915,5 +932,47 @@ extern "C" int mr1l_reconstruct_noalloc(mr1l_plan_t* plan, const void* y, int nr
     blue_run(lw.geom, io, kModeRecon, nrhs, s);
     gather(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, Cbuf, sumM, nrhs, (cplx*)c, plan->nI,
            nullptr, nullptr, s);
+  });
+}
+
+extern "C" int mr1l_lattice_noise(uint64_t seed, int t, int rep, int L, const int64_t* M, double sigma, void* y,
+                                  void* stream) {
+  return guarded([&] {
+    MR1L_REQUIRE(L >= 1 && L <= 64 && M != nullptr && y != nullptr, "bad arguments");
+    MR1L_REQUIRE(((uintptr_t)y & 15) == 0, "y must be 16-byte aligned");
+    MR1L_REQUIRE(sigma >= 0.0, "sigma must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int> Mh(L);
+    std::vector<int64_t> offh(L);
+    int64_t sum = 0;
+    for (int l = 0; l < L; ++l) {
+      MR1L_REQUIRE(M[l] >= 1 && M[l] < (int64_t(1) << 31), "M_l out of range");
+      Mh[l] = (int)M[l];
+      offh[l] = sum;
+      sum += M[l];
+    }
+    DevBuf<int> Md;
+    DevBuf<int64_t> offd;
+    Md.reserve(L);
+    offd.reserve(L);
+    MR1L_CUDA(cudaMemcpyAsync(Md.get(), Mh.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
+    MR1L_CUDA(cudaMemcpyAsync(offd.get(), offh.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MR1L_CUDA(cudaMemsetAsync(y, 0, sum * sizeof(cplx), s));
+    BlueGeom g{};
+    g.L = L;
+    g.M = Md.get();
+    g.off = offd.get();
+    g.sum_M = sum;
+    g.P = 2 * (int)*std::max_element(Mh.begin(), Mh.end());
+    BlueIO io{};
+    io.out = (cplx*)y;
+    io.out_stride = sum;
+    io.noise_scale = sigma / std::sqrt(2.0);
+    io.noise_seed = seed;
+    io.noise_t = t;
+    io.noise_rep = rep;
+    io.noise_rep_per_rhs = 1;
+    add_lattice_noise(g, io, 1, s);
+    MR1L_CUDA(cudaStreamSynchronize(s));
   });
 }

@@ -1,4 +1,4 @@
-// Bluestein prime-length DFTs over power-of-two FP64 FFTs.
+// Bluestein prime-length DFTs over FFTs of length 2^k or 3 * 2^k.
 //
 // A length-M DFT X[r] = sum_j x[j] exp(-2 pi i j r / M) (Algorithm 2, one
 // lattice) is rewritten with j r = (j^2 + r^2 - (r - j)^2) / 2 as
@@ -8,7 +8,9 @@
 //
 // On GB300 the FP64 pipe (about 2 FMA per clock per SM) bounds these
 // transforms, so the kernels read chirps, filters and twiddles from tables
-// instead of recomputing them, and never spend FP64 work on index math.
+// instead of recomputing them, and never spend FP64 work on index math.  The
+// same kernels also run in double-float arithmetic (arith.cuh), which moves
+// the butterflies to the FP32 pipes (about 60 times the FP64 rate).
 //
 // Structure: P <= 4096 runs in one CTA per transform (everything in shared
 // memory).  Larger P uses the 4-step split P = P1 * P2 without transposes:
@@ -18,129 +20,120 @@
 //                     times the filter spectrum (stored in the same order),
 //                     inverse FFT_P2, times w_P^(-n2 k1);
 //   pass 3 (columns): inverse FFT_P1 over k1, natural order x[n1 P2 + n2].
-// Each sub-FFT is a mixed-radix (8, 4, 2) Stockham autosort FFT in shared
+// Each sub-FFT is a mixed-radix (8, 4, 2, 3) Stockham autosort FFT in shared
 // memory (Govindaraju et al., SC'08 formulation).
 #include <map>
 #include <mutex>
+#include <string>
+#include <type_traits>
 
 #include <cmath>
 
+#include "arith.cuh"
 #include "fft.cuh"
 #include "prof.cuh"
 
 namespace mr1l {
 
 // ---------------------------------------------------------------------------
-// Register DFTs of size 2, 4, 8 (forward: exp(-2 pi i / R); INV: conjugate).
+// Register DFTs of size 2, 3, 4, 8 (forward: exp(-2 pi i / R); INV: conjugate)
+// over an arithmetic O (OpsF64 or OpsDF).
 // ---------------------------------------------------------------------------
-template <int R, bool INV>
+template <int R, bool INV, class O>
 struct RegDft;
 
-template <bool INV>
-struct RegDft<2, INV> {
-  static __device__ __forceinline__ void run(cplx* v) {
-    cplx a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+template <bool INV, class O>
+struct RegDft<2, INV, O> {
+  typedef typename O::V V;
+  static __device__ __forceinline__ void run(V* v) {
+    V a = v[0], b = v[1];
+    v[0] = O::add(a, b);
+    v[1] = O::sub(a, b);
   }
 };
 
-template <bool INV>
-struct RegDft<4, INV> {
-  static __device__ __forceinline__ void run(cplx* v) {
-    cplx t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    cplx t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
-    v[0] = cadd(t0, t2);
-    v[2] = csub(t0, t2);
-    v[1] = cadd(t1, t3);
-    v[3] = csub(t1, t3);
+template <bool INV, class O>
+struct RegDft<4, INV, O> {
+  typedef typename O::V V;
+  static __device__ __forceinline__ void run(V* v) {
+    V t0 = O::add(v[0], v[2]), t1 = O::sub(v[0], v[2]);
+    V t2 = O::add(v[1], v[3]), t3 = O::template mi<INV>(O::sub(v[1], v[3]));
+    v[0] = O::add(t0, t2);
+    v[2] = O::sub(t0, t2);
+    v[1] = O::add(t1, t3);
+    v[3] = O::sub(t1, t3);
   }
 };
 
-template <bool INV>
-struct RegDft<8, INV> {
-  static __device__ __forceinline__ void run(cplx* v) {
-    const double h = 0.70710678118654752440;  // 1/sqrt(2)
-    cplx e[4] = {v[0], v[2], v[4], v[6]};
-    cplx o[4] = {v[1], v[3], v[5], v[7]};
-    RegDft<4, INV>::run(e);
-    RegDft<4, INV>::run(o);
-    // X_k = E_k + w8^k O_k, X_{k+4} = E_k - w8^k O_k; the 1/sqrt(2) of w8 and
-    // w8^3 is folded into fused multiply-adds
-    cplx a = o[1], c = o[3];
-    double a1x, a1y, a3x, a3y;  // w8 O_1 and w8^3 O_3 without the factor h
-    if (!INV) {
-      a1x = a.x + a.y;
-      a1y = a.y - a.x;
-      a3x = c.y - c.x;
-      a3y = -(c.x + c.y);
-    } else {
-      a1x = a.x - a.y;
-      a1y = a.x + a.y;
-      a3x = -(c.x + c.y);
-      a3y = c.x - c.y;
-    }
-    cplx o2 = mul_mi<INV>(o[2]);
-    v[0] = cadd(e[0], o[0]);
-    v[4] = csub(e[0], o[0]);
-    v[1] = cmake(fma(h, a1x, e[1].x), fma(h, a1y, e[1].y));
-    v[5] = cmake(fma(-h, a1x, e[1].x), fma(-h, a1y, e[1].y));
-    v[2] = cadd(e[2], o2);
-    v[6] = csub(e[2], o2);
-    v[3] = cmake(fma(h, a3x, e[3].x), fma(h, a3y, e[3].y));
-    v[7] = cmake(fma(-h, a3x, e[3].x), fma(-h, a3y, e[3].y));
+// w8 = exp(-+ 2 pi i / 8): w8 x = (x + mi(x)) / sqrt2, w8^3 x = (mi(x) - x) / sqrt2
+template <bool INV, class O>
+__device__ __forceinline__ typename O::V w8_1(typename O::V x) {
+  return O::scale(O::add(x, O::template mi<INV>(x)), 0.70710678118654752440);
+}
+template <bool INV, class O>
+__device__ __forceinline__ typename O::V w8_3(typename O::V x) {
+  return O::scale(O::sub(O::template mi<INV>(x), x), 0.70710678118654752440);
+}
+
+template <bool INV, class O>
+struct RegDft<8, INV, O> {
+  typedef typename O::V V;
+  static __device__ __forceinline__ void run(V* v) {
+    V e[4] = {v[0], v[2], v[4], v[6]};
+    V o[4] = {v[1], v[3], v[5], v[7]};
+    RegDft<4, INV, O>::run(e);
+    RegDft<4, INV, O>::run(o);
+    V o1 = w8_1<INV, O>(o[1]);
+    V o2 = O::template mi<INV>(o[2]);
+    V o3 = w8_3<INV, O>(o[3]);
+    v[0] = O::add(e[0], o[0]);
+    v[4] = O::sub(e[0], o[0]);
+    v[1] = O::add(e[1], o1);
+    v[5] = O::sub(e[1], o1);
+    v[2] = O::add(e[2], o2);
+    v[6] = O::sub(e[2], o2);
+    v[3] = O::add(e[3], o3);
+    v[7] = O::sub(e[3], o3);
   }
 };
 
 // Radix 3: X0 = a + b + c, X1,2 = a - (b + c)/2 -+ i (sqrt(3)/2)(b - c) (forward).
-template <bool INV>
-struct RegDft<3, INV> {
-  static __device__ __forceinline__ void run(cplx* v) {
-    const double s3 = 0.86602540378443864676;  // sqrt(3)/2
-    cplx t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
-    cplx a = v[0];
-    v[0] = cadd(a, t1);
-    cplx m1 = cmake(fma(-0.5, t1.x, a.x), fma(-0.5, t1.y, a.y));
-    // forward: -i s3 t2 ; inverse: +i s3 t2
-    cplx m2 = INV ? cmake(-s3 * t2.y, s3 * t2.x) : cmake(s3 * t2.y, -s3 * t2.x);
-    v[1] = cadd(m1, m2);
-    v[2] = csub(m1, m2);
+template <bool INV, class O>
+struct RegDft<3, INV, O> {
+  typedef typename O::V V;
+  static __device__ __forceinline__ void run(V* v) {
+    V t1 = O::add(v[1], v[2]), t2 = O::sub(v[1], v[2]);
+    V a = v[0];
+    v[0] = O::add(a, t1);
+    V m1 = O::sub(a, O::scale(t1, 0.5));
+    V m2 = O::scale(O::template mi<INV>(t2), 0.86602540378443864676);
+    v[1] = O::add(m1, m2);
+    v[2] = O::sub(m1, m2);
   }
 };
 
 // Radix-8 DFT of a sequence whose inputs 4..7 are zero (the first stage of a
-// zero-padded Bluestein input): v[0..3] in, v[0..7] out, 36 FP64 operations
-// instead of 52.
-template <bool INV>
-__device__ __forceinline__ void reg_dft8_half(cplx* v) {
-  const double h = 0.70710678118654752440;
-  cplx e0 = cadd(v[0], v[2]), e2 = csub(v[0], v[2]);
-  cplx m2 = mul_mi<INV>(v[2]);
-  cplx e1 = cadd(v[0], m2), e3 = csub(v[0], m2);
-  cplx o0 = cadd(v[1], v[3]), o2 = csub(v[1], v[3]);
-  cplx m3 = mul_mi<INV>(v[3]);
-  cplx o1 = cadd(v[1], m3), o3 = csub(v[1], m3);
-  double a1x, a1y, a3x, a3y;
-  if (!INV) {
-    a1x = o1.x + o1.y;
-    a1y = o1.y - o1.x;
-    a3x = o3.y - o3.x;
-    a3y = -(o3.x + o3.y);
-  } else {
-    a1x = o1.x - o1.y;
-    a1y = o1.x + o1.y;
-    a3x = -(o3.x + o3.y);
-    a3y = o3.x - o3.y;
-  }
-  o2 = mul_mi<INV>(o2);
-  v[0] = cadd(e0, o0);
-  v[4] = csub(e0, o0);
-  v[1] = cmake(fma(h, a1x, e1.x), fma(h, a1y, e1.y));
-  v[5] = cmake(fma(-h, a1x, e1.x), fma(-h, a1y, e1.y));
-  v[2] = cadd(e2, o2);
-  v[6] = csub(e2, o2);
-  v[3] = cmake(fma(h, a3x, e3.x), fma(h, a3y, e3.y));
-  v[7] = cmake(fma(-h, a3x, e3.x), fma(-h, a3y, e3.y));
+// zero-padded Bluestein input): v[0..3] in, v[0..7] out.
+template <bool INV, class O>
+__device__ __forceinline__ void reg_dft8_half(typename O::V* v) {
+  typedef typename O::V V;
+  V e0 = O::add(v[0], v[2]), e2 = O::sub(v[0], v[2]);
+  V m2 = O::template mi<INV>(v[2]);
+  V e1 = O::add(v[0], m2), e3 = O::sub(v[0], m2);
+  V o0 = O::add(v[1], v[3]), o2 = O::sub(v[1], v[3]);
+  V m3 = O::template mi<INV>(v[3]);
+  V o1 = O::add(v[1], m3), o3 = O::sub(v[1], m3);
+  o1 = w8_1<INV, O>(o1);
+  o2 = O::template mi<INV>(o2);
+  o3 = w8_3<INV, O>(o3);
+  v[0] = O::add(e0, o0);
+  v[4] = O::sub(e0, o0);
+  v[1] = O::add(e1, o1);
+  v[5] = O::sub(e1, o1);
+  v[2] = O::add(e2, o2);
+  v[6] = O::sub(e2, o2);
+  v[3] = O::add(e3, o3);
+  v[7] = O::sub(e3, o3);
 }
 
 // ---------------------------------------------------------------------------
@@ -152,13 +145,14 @@ __device__ __forceinline__ void reg_dft8_half(cplx* v) {
 //   else: element index fastest (row tiles, is == 1)
 // HALF (first radix-8 stage only): inputs r >= 4 are known zeros.
 // ---------------------------------------------------------------------------
-template <int R, bool INV, bool COLS, bool HALF = false>
-__device__ __forceinline__ void stockham_stage(cplx* s, int n, int Ns, int nseq, int bs, int is,
-                                               const cplx* twn_n) {
+template <int R, bool INV, bool COLS, class O, bool HALF = false>
+__device__ __forceinline__ void stockham_stage(typename O::V* s, int n, int Ns, int nseq, int bs, int is,
+                                               const typename O::V* twn_n) {
+  typedef typename O::V V;
   constexpr int CNT = (8 + R - 1) / R;
   const int nb = n / R;
   const int total = nseq * nb;
-  cplx v[CNT][R];
+  V v[CNT][R];
   int base[CNT];
   bool act[CNT];
 #pragma unroll
@@ -176,23 +170,23 @@ __device__ __forceinline__ void stockham_stage(cplx* s, int n, int Ns, int nseq,
     int k = j % Ns;
     base[c] = b * bs + ((j - k) * R + k) * is;
     if (act[c] && HALF) {
-      const cplx* src = s + b * bs + j * is;
+      const V* src = s + b * bs + j * is;
 #pragma unroll
       for (int r = 0; r < 4; ++r) v[c][r] = src[r * nb * is];
-      reg_dft8_half<INV>(v[c]);
+      reg_dft8_half<INV, O>(v[c]);
     } else if (act[c]) {
-      const cplx* src = s + b * bs + j * is;
+      const V* src = s + b * bs + j * is;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[c][r] = src[r * nb * is];
       if (Ns > 1) {
         int step = k * (n / (Ns * R));
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          cplx w = twn_n[r * step];
-          v[c][r] = INV ? cmulc(v[c][r], w) : cmul(v[c][r], w);
+          V w = twn_n[r * step];
+          v[c][r] = INV ? O::mulc(v[c][r], w) : O::mul(v[c][r], w);
         }
       }
-      RegDft<R, INV>::run(v[c]);
+      RegDft<R, INV, O>::run(v[c]);
     }
   }
   __syncthreads();
@@ -207,7 +201,8 @@ __device__ __forceinline__ void stockham_stage(cplx* s, int n, int Ns, int nseq,
 }
 
 // Twiddles exp(-2 pi i e / n) of a sub-FFT length n (2^a or 3 * 2^a).
-__device__ __forceinline__ const cplx* twiddles_of(const cplx* twn, int n) {
+template <class T>
+__device__ __forceinline__ const T* twiddles_of(const T* twn, int n) {
   return (n & (n - 1)) == 0 ? twn + n : twn + 8192 + n - 3;
 }
 
@@ -215,48 +210,71 @@ __device__ __forceinline__ const cplx* twiddles_of(const cplx* twn, int n) {
 // or radix-2 stage for the rest of 2^a, then radix 3.  Natural order in and
 // out.  HALF_FIRST: the upper half of every input sequence is zero (needs
 // 8 | n).
-template <bool INV, bool COLS, bool HALF_FIRST = false>
-__device__ __forceinline__ void smem_fft(cplx* s, int n, int nseq, int bs, int is, const cplx* twn) {
-  const cplx* twn_n = twiddles_of(twn, n);
+template <bool INV, bool COLS, class O, bool HALF_FIRST = false>
+__device__ __forceinline__ void smem_fft(typename O::V* s, int n, int nseq, int bs, int is,
+                                         const typename O::V* twn) {
+  const typename O::V* twn_n = twiddles_of(twn, n);
   const bool three = (n % 3) == 0;
   int rem = 31 - __clz(three ? n / 3 : n);  // log2 of the power-of-two part
   int Ns = 1;
   if (HALF_FIRST && rem >= 3) {
-    stockham_stage<8, INV, COLS, true>(s, n, Ns, nseq, bs, is, twn_n);
+    stockham_stage<8, INV, COLS, O, true>(s, n, Ns, nseq, bs, is, twn_n);
     Ns <<= 3;
     rem -= 3;
   }
   while (rem >= 3) {
-    stockham_stage<8, INV, COLS>(s, n, Ns, nseq, bs, is, twn_n);
+    stockham_stage<8, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n);
     Ns <<= 3;
     rem -= 3;
   }
   if (rem == 2) {
-    stockham_stage<4, INV, COLS>(s, n, Ns, nseq, bs, is, twn_n);
+    stockham_stage<4, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n);
     Ns <<= 2;
   }
   if (rem == 1) {
-    stockham_stage<2, INV, COLS>(s, n, Ns, nseq, bs, is, twn_n);
+    stockham_stage<2, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n);
     Ns <<= 1;
   }
-  if (three) stockham_stage<3, INV, COLS>(s, n, Ns, nseq, bs, is, twn_n);
+  if (three) stockham_stage<3, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n);
 }
+
+// ---------------------------------------------------------------------------
+// Tables in the arithmetic's format
+// ---------------------------------------------------------------------------
+template <class O>
+struct Tab;
+template <>
+struct Tab<OpsF64> {
+  static __device__ __forceinline__ const cplx* w(const BlueGeom& g) { return g.w; }
+  static __device__ __forceinline__ const cplx* ws(const BlueGeom& g) { return g.ws; }
+  static __device__ __forceinline__ const cplx* tw(const BlueGeom& g) { return g.tw; }
+  static __device__ __forceinline__ const cplx* twn(const BlueGeom& g) { return g.twn; }
+  static __device__ __forceinline__ cplx* Bh(const BlueGeom& g) { return g.Bh; }
+};
+template <>
+struct Tab<OpsDF> {
+  static __device__ __forceinline__ const float4* w(const BlueGeom& g) { return g.w_df; }
+  static __device__ __forceinline__ const float4* ws(const BlueGeom& g) { return g.ws_df; }
+  static __device__ __forceinline__ const float4* tw(const BlueGeom& g) { return g.tw_df; }
+  static __device__ __forceinline__ const float4* twn(const BlueGeom& g) { return g.twn_df; }
+  static __device__ __forceinline__ float4* Bh(const BlueGeom& g) { return (float4*)g.Bh; }
+};
 
 // ---------------------------------------------------------------------------
 // Sources and sinks
 // ---------------------------------------------------------------------------
-template <int MODE>
-__device__ __forceinline__ cplx load_input(const BlueGeom& g, const BlueIO& io, int l, int h, int M,
-                                           int64_t off, int64_t n) {
+template <int MODE, class O>
+__device__ __forceinline__ typename O::V load_input(const BlueGeom& g, const BlueIO& io, int h, int M,
+                                                    int64_t off, int64_t n) {
   if (MODE == kModeFilter) {
-    if (n < M) return cconj(g.w[off + n]);
-    if (n > g.P - M) return cconj(g.w[off + (g.P - n)]);
-    return cmake(0.0, 0.0);
+    if (n < M) return O::conj(Tab<O>::w(g)[off + n]);
+    if (n > g.P - M) return O::conj(Tab<O>::w(g)[off + (g.P - n)]);
+    return O::zero();
   }
-  if (n >= M) return cmake(0.0, 0.0);
-  cplx x = io.in[h * io.in_stride + off + n];
-  if (MODE == kModeRecon) return cmul(x, g.ws[off + n]);
-  return cmul(cconj(x), g.w[off + n]);
+  if (n >= M) return O::zero();
+  typename O::V x = O::from(io.in[h * io.in_stride + off + n]);
+  if (MODE == kModeRecon) return O::mul(x, Tab<O>::ws(g)[off + n]);
+  return O::mul(O::conj(x), Tab<O>::w(g)[off + n]);
 }
 
 __device__ __forceinline__ cplx lattice_noise(uint64_t seed, int t, int rep, int l, int64_t j, double scale) {
@@ -270,28 +288,23 @@ __device__ __forceinline__ cplx lattice_noise(uint64_t seed, int t, int rep, int
   return cmake(scale * (R * cs), scale * (R * sn));
 }
 
-template <int MODE>
-__device__ __forceinline__ void store_output(const BlueGeom& g, const BlueIO& io, int l, int h, int64_t off,
-                                             int64_t n, cplx v) {
-  if (MODE == kModeRecon) {
-    io.out[h * io.out_stride + off + n] = v;
-  } else {
-    cplx y = cconj(cmul(g.w[off + n], v));
-    if (io.noise_scale != 0.0) {
-      cplx e = lattice_noise(io.noise_seed, io.noise_t, io.noise_rep + h * io.noise_rep_per_rhs, l, n,
-                             io.noise_scale);
-      y = cadd(y, e);
-    }
-    io.out[h * io.out_stride + off + n] = y;
-  }
+template <int MODE, class O>
+__device__ __forceinline__ void store_output(const BlueGeom& g, const BlueIO& io, int h, int64_t off, int64_t n,
+                                             typename O::V v) {
+  if (MODE == kModeRecon)
+    io.out[h * io.out_stride + off + n] = O::to(v);
+  else
+    io.out[h * io.out_stride + off + n] = O::to(O::conj(O::mul(Tab<O>::w(g)[off + n], v)));
 }
 
 // ---------------------------------------------------------------------------
 // P <= 4096: the whole convolution in one CTA.
 // ---------------------------------------------------------------------------
-template <int MODE>
+template <int MODE, class O>
 __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) {
-  extern __shared__ cplx sm[];
+  typedef typename O::V V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = (V*)smraw;
   const int gi = blockIdx.x;
   const int l = gi % g.L, h = gi / g.L;
   const int P = g.P, M = g.M[l];
@@ -300,22 +313,22 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
   // upper half is never loaded and the first radix-8 stage skips it
   const bool half = MODE != kModeFilter && (P % 8) == 0;
   const int nload = half ? P / 2 : P;
-  for (int n = threadIdx.x; n < nload; n += blockDim.x) sm[n] = load_input<MODE>(g, io, l, h, M, off, n);
+  for (int n = threadIdx.x; n < nload; n += blockDim.x) sm[n] = load_input<MODE, O>(g, io, h, M, off, n);
   __syncthreads();
   if (half)
-    smem_fft<false, false, true>(sm, P, 1, 0, 1, g.twn);
+    smem_fft<false, false, O, true>(sm, P, 1, 0, 1, Tab<O>::twn(g));
   else
-    smem_fft<false, false>(sm, P, 1, 0, 1, g.twn);
-  cplx* Bh = g.Bh + (int64_t)l * P;
+    smem_fft<false, false, O>(sm, P, 1, 0, 1, Tab<O>::twn(g));
+  V* Bh = Tab<O>::Bh(g) + (int64_t)l * P;
   if (MODE == kModeFilter) {
-    const double sc = 1.0 / (double)P;  // exact: P is a power of two
-    for (int n = threadIdx.x; n < P; n += blockDim.x) Bh[n] = cmake(sm[n].x * sc, sm[n].y * sc);
+    const double sc = 1.0 / (double)P;
+    for (int n = threadIdx.x; n < P; n += blockDim.x) Bh[n] = O::scale(sm[n], sc);
     return;
   }
-  for (int n = threadIdx.x; n < P; n += blockDim.x) sm[n] = cmul(sm[n], Bh[n]);
+  for (int n = threadIdx.x; n < P; n += blockDim.x) sm[n] = O::mul(sm[n], Bh[n]);
   __syncthreads();
-  smem_fft<true, false>(sm, P, 1, 0, 1, g.twn);
-  for (int n = threadIdx.x; n < M; n += blockDim.x) store_output<MODE>(g, io, l, h, off, n, sm[n]);
+  smem_fft<true, false, O>(sm, P, 1, 0, 1, Tab<O>::twn(g));
+  for (int n = threadIdx.x; n < M; n += blockDim.x) store_output<MODE, O>(g, io, h, off, n, sm[n]);
 }
 
 // ---------------------------------------------------------------------------
@@ -323,7 +336,7 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
 // ---------------------------------------------------------------------------
 // Tiles of 2048 complex (32 KB shared memory, 256 threads) so that three CTAs
 // share an SM and hide each other's load and barrier phases; a single
-// column or row of 4096 takes a 4096-element tile.
+// column or row of more than 2048 takes a tile of its own length.
 constexpr int kTileElems = 2048;
 __host__ __device__ __forceinline__ int col_tile(int P1) {
   int cb = kTileElems / P1;  // P1 = 3 * 2^a gives a tile of 3/4 x 2048
@@ -339,9 +352,11 @@ __host__ __device__ __forceinline__ int row_tile(int P2) {
 }
 
 // Pass 1: columns, forward, with the 4-step twiddle.
-template <int MODE>
+template <int MODE, class O>
 __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io) {
-  extern __shared__ cplx sm[];
+  typedef typename O::V V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = (V*)smraw;
   const int gi = blockIdx.y;
   const int l = gi % g.L, h = gi / g.L;
   const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1);
@@ -352,73 +367,77 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
   const int rows = MODE == kModeFilter ? P1 : P1 / 2;
   for (int e = threadIdx.x; e < rows * CB; e += blockDim.x) {
     int i = e / CB, b = e - i * CB;
-    sm[e] = load_input<MODE>(g, io, l, h, M, off, (int64_t)i * P2 + n2_0 + b);
+    sm[e] = load_input<MODE, O>(g, io, h, M, off, (int64_t)i * P2 + n2_0 + b);
   }
   __syncthreads();
   if (MODE == kModeFilter)
-    smem_fft<false, true>(sm, P1, CB, 1, CB, g.twn);
+    smem_fft<false, true, O>(sm, P1, CB, 1, CB, Tab<O>::twn(g));
   else
-    smem_fft<false, true, true>(sm, P1, CB, 1, CB, g.twn);
-  cplx* work = io.work + (int64_t)gi * P;
+    smem_fft<false, true, O, true>(sm, P1, CB, 1, CB, Tab<O>::twn(g));
+  V* work = (V*)io.work + (int64_t)gi * P;
+  const V* tw = Tab<O>::tw(g);
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int k1 = e / CB, b = e - k1 * CB;
     int n2 = n2_0 + b;
-    cplx w = g.tw[((int64_t)n2 * k1) % P];
-    work[(int64_t)k1 * P2 + n2] = cmul(sm[e], w);
+    work[(int64_t)k1 * P2 + n2] = O::mul(sm[e], tw[((int64_t)n2 * k1) % P]);
   }
 }
 
 // Pass 2: rows.  FILTER: forward FFT scaled by 1/P into Bh.  Otherwise forward
 // FFT, times Bh, inverse FFT, times conj(w_P^(n2 k1)).
-template <bool FILTER>
+template <bool FILTER, class O>
 __global__ void __launch_bounds__(512) blue_row_kernel(BlueGeom g, BlueIO io) {
-  extern __shared__ cplx sm[];
+  typedef typename O::V V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = (V*)smraw;
   const int gi = blockIdx.y;
   const int l = gi % g.L;
   const int P = g.P, P2 = g.P2, RB = row_tile(P2);
   const int k1_0 = blockIdx.x * RB;
-  cplx* work = io.work + (int64_t)gi * P + (int64_t)k1_0 * P2;
+  V* work = (V*)io.work + (int64_t)gi * P + (int64_t)k1_0 * P2;
   for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = work[e];
   __syncthreads();
-  smem_fft<false, false>(sm, P2, RB, P2, 1, g.twn);
-  cplx* Bh = g.Bh + (int64_t)l * P + (int64_t)k1_0 * P2;
+  smem_fft<false, false, O>(sm, P2, RB, P2, 1, Tab<O>::twn(g));
+  V* Bh = Tab<O>::Bh(g) + (int64_t)l * P + (int64_t)k1_0 * P2;
   if (FILTER) {
     const double sc = 1.0 / (double)P;
-    for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) Bh[e] = cmake(sm[e].x * sc, sm[e].y * sc);
+    for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) Bh[e] = O::scale(sm[e], sc);
     return;
   }
-  for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = cmul(sm[e], Bh[e]);
+  for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = O::mul(sm[e], Bh[e]);
   __syncthreads();
-  smem_fft<true, false>(sm, P2, RB, P2, 1, g.twn);
+  smem_fft<true, false, O>(sm, P2, RB, P2, 1, Tab<O>::twn(g));
+  const V* tw = Tab<O>::tw(g);
   for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) {
     int b = e / P2, n2 = e - b * P2;
     int k1 = k1_0 + b;
-    cplx w = g.tw[((int64_t)n2 * k1) % P];
-    work[e] = cmulc(sm[e], w);
+    work[e] = O::mulc(sm[e], tw[((int64_t)n2 * k1) % P]);
   }
 }
 
 // Pass 3: columns, inverse; natural-order output n = n1 P2 + n2 for n < M.
-template <int MODE>
+template <int MODE, class O>
 __global__ void __launch_bounds__(512) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
-  extern __shared__ cplx sm[];
+  typedef typename O::V V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = (V*)smraw;
   const int gi = blockIdx.y;
   const int l = gi % g.L, h = gi / g.L;
   const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1);
   const int M = g.M[l];
   const int64_t off = g.off[l];
   const int n2_0 = blockIdx.x * CB;
-  const cplx* work = io.work + (int64_t)gi * P;
+  const V* work = (const V*)io.work + (int64_t)gi * P;
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int k1 = e / CB, b = e - k1 * CB;
     sm[e] = work[(int64_t)k1 * P2 + n2_0 + b];
   }
   __syncthreads();
-  smem_fft<true, true>(sm, P1, CB, 1, CB, g.twn);
+  smem_fft<true, true, O>(sm, P1, CB, 1, CB, Tab<O>::twn(g));
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int n1 = e / CB, b = e - n1 * CB;
     int64_t n = (int64_t)n1 * P2 + n2_0 + b;
-    if (n < M) store_output<MODE>(g, io, l, h, off, n, sm[e]);
+    if (n < M) store_output<MODE, O>(g, io, h, off, n, sm[e]);
   }
 }
 
@@ -503,6 +522,52 @@ const cplx* small_twiddles(cudaStream_t s) {
   return p;
 }
 
+__global__ void to_df_kernel(const cplx* src, float4* dst, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = OpsDF::from(src[i]);
+}
+
+void to_double_float(const cplx* src, float4* dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  MR1L_LAUNCH("to_df_kernel", s, 0, 32.0 * n, to_df_kernel<<<cdiv(n, 256), 256, 0, s>>>(src, dst, n));
+}
+
+namespace {
+std::map<std::pair<int, int>, float4*> g_tw_df;  // (device, P) -> table
+std::map<int, float4*> g_twn_df;
+}  // namespace
+
+const float4* twiddle_table_df(int Pn, cudaStream_t s) {
+  const cplx* src = twiddle_table(Pn, s);
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto key = std::make_pair(dev, Pn);
+  auto it = g_tw_df.find(key);
+  if (it != g_tw_df.end()) return it->second;
+  float4* p = nullptr;
+  MR1L_CUDA(cudaMalloc(&p, (size_t)Pn * sizeof(float4)));
+  to_double_float(src, p, Pn, s);
+  MR1L_CUDA(cudaStreamSynchronize(s));
+  g_tw_df[key] = p;
+  return p;
+}
+
+const float4* small_twiddles_df(cudaStream_t s) {
+  const cplx* src = small_twiddles(s);
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto it = g_twn_df.find(dev);
+  if (it != g_twn_df.end()) return it->second;
+  float4* p = nullptr;
+  MR1L_CUDA(cudaMalloc(&p, kSmallTw * sizeof(float4)));
+  to_double_float(src, p, kSmallTw, s);
+  MR1L_CUDA(cudaStreamSynchronize(s));
+  g_twn_df[dev] = p;
+  return p;
+}
+
 int blue_length(int64_t n) {
   int64_t p2 = 1;
   while (p2 < n) p2 <<= 1;
@@ -552,17 +617,23 @@ static double fft_flops(double n) { return n > 1 ? 5.0 * n * std::log2(n) : 0.0;
 
 // Algorithmic work of one launch (FFT flops by the 5 n log2 n convention plus
 // 6 flops per complex multiply; bytes that the pass must move).
-template <int MODE>
+template <int MODE, class O>
 static void launch_first_last(const BlueGeom& g, const BlueIO& io, int ntrans, cudaStream_t s) {
+  const bool df = std::is_same<O, OpsDF>::value;
   const double P = g.P, nr = (double)ntrans / g.L, sumM = (double)g.sum_M;
   const double cb = sizeof(cplx);
+  const char* sfx = MODE == kModeFilter ? "filter" : (MODE == kModeRecon ? "recon" : "eval");
+  std::string nm;
+  auto name = [&](const char* pass) {
+    nm = std::string("blue_") + pass + "_" + sfx + (df ? "_df" : "");
+    return nm.c_str();
+  };
   if (g.P <= kSmallMax) {
     size_t smem = (size_t)g.P * sizeof(cplx);
-    set_smem(blue_small_kernel<MODE>, smem);
+    set_smem(blue_small_kernel<MODE, O>, smem);
     double fl = ntrans * (MODE == kModeFilter ? fft_flops(P) : 2 * fft_flops(P) + 6 * P) + nr * 6 * sumM;
     double by = MODE == kModeFilter ? g.L * P * cb + sumM * cb : nr * sumM * cb * 3 + ntrans * P * cb;
-    MR1L_LAUNCH(MODE == kModeFilter ? "blue_small_filter" : (MODE == kModeRecon ? "blue_small_recon" : "blue_small_eval"),
-                s, fl, by, blue_small_kernel<MODE><<<ntrans, threads_for(g.P), smem, s>>>(g, io));
+    MR1L_LAUNCH(name("small"), s, fl, by, blue_small_kernel<MODE, O><<<ntrans, threads_for(g.P), smem, s>>>(g, io));
     return;
   }
   int CB = col_tile(g.P1), RB = row_tile(g.P2);
@@ -570,25 +641,23 @@ static void launch_first_last(const BlueGeom& g, const BlueIO& io, int ntrans, c
   size_t smem_r = (size_t)RB * g.P2 * sizeof(cplx);
   dim3 gc(g.P2 / CB, ntrans), gr(g.P1 / RB, ntrans);
   const double P1 = g.P1, P2 = g.P2;
-  set_smem(blue_col_fwd_kernel<MODE>, smem_c);
-  MR1L_LAUNCH(MODE == kModeFilter ? "blue_col_fwd_filter" : (MODE == kModeRecon ? "blue_col_fwd_recon" : "blue_col_fwd_eval"),
-              s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM, nr * sumM * cb * 2 + ntrans * P * cb,
-              blue_col_fwd_kernel<MODE><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
+  set_smem(blue_col_fwd_kernel<MODE, O>, smem_c);
+  MR1L_LAUNCH(name("col_fwd"), s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM,
+              nr * sumM * cb * 2 + ntrans * P * cb,
+              blue_col_fwd_kernel<MODE, O><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
   if (MODE == kModeFilter) {
-    set_smem(blue_row_kernel<true>, smem_r);
-    MR1L_LAUNCH("blue_row_filter", s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
-                blue_row_kernel<true><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
+    set_smem(blue_row_kernel<true, O>, smem_r);
+    MR1L_LAUNCH(name("row"), s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
+                blue_row_kernel<true, O><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
     return;
   }
-  set_smem(blue_row_kernel<false>, smem_r);
-  MR1L_LAUNCH(MODE == kModeRecon ? "blue_row_recon" : "blue_row_eval", s,
-              ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
-              blue_row_kernel<false><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
-  set_smem(blue_col_inv_kernel<MODE>, smem_c);
-  MR1L_LAUNCH(MODE == kModeRecon ? "blue_col_inv_recon" : "blue_col_inv_eval", s,
-              ntrans * P2 * fft_flops(P1) + (MODE == kModeEval ? nr * 6 * sumM : 0.0),
+  set_smem(blue_row_kernel<false, O>, smem_r);
+  MR1L_LAUNCH(name("row"), s, ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
+              blue_row_kernel<false, O><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
+  set_smem(blue_col_inv_kernel<MODE, O>, smem_c);
+  MR1L_LAUNCH(name("col_inv"), s, ntrans * P2 * fft_flops(P1) + (MODE == kModeEval ? nr * 6 * sumM : 0.0),
               ntrans * P * cb + nr * sumM * cb * (MODE == kModeEval ? 2 : 1),
-              blue_col_inv_kernel<MODE><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
+              blue_col_inv_kernel<MODE, O><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
 }
 
 void blue_filter(const BlueGeom& g, cudaStream_t s) {
@@ -597,16 +666,157 @@ void blue_filter(const BlueGeom& g, cudaStream_t s) {
   // row by row; each row is read completely before it is written)
   BlueIO io{};
   io.work = g.Bh;
-  launch_first_last<kModeFilter>(g, io, g.L, s);
+  if (g.df)
+    launch_first_last<kModeFilter, OpsDF>(g, io, g.L, s);
+  else
+    launch_first_last<kModeFilter, OpsF64>(g, io, g.L, s);
+}
+
+// ---------------------------------------------------------------------------
+// Lattice noise: y[h][off_l + j] += sigma/sqrt(2) (g1 + i g2) by Box-Muller on
+// the Philox words of sample j (purpose 5; node 0 shared by all lattices).
+//
+// The logarithm and the sine/cosine are table driven so that the FP64 pipe
+// does little work per sample:
+//   ln u = E ln2 + ln c_k + log1p(r),  u = 2^E m with m in [3/4, 3/2),
+//     c_k = 1 + trunc(128 (m - 1)) / 128 (so c = 1 for m near 1 and the result
+//     keeps its relative accuracy there), r = (m - c_k) / c_k with m - c_k
+//     exact, |r| < 1/96, log1p by its Taylor series to degree 9 (Tang's
+//     table-driven logarithm, ACM TOMS 16(4), 1990);
+//   2 pi u = 2 pi q / 256 + x,  x in [0, 2 pi / 256): sin and cos of x by
+//     their Taylor series (degrees 7 and 8), combined with the tabulated
+//     sin / cos of 2 pi q / 256 by the angle-addition formulas.
+// Both stay within a few units in the last place of FP64.
+// ---------------------------------------------------------------------------
+constexpr int kLnTab = 96, kScTab = 256;
+
+struct NoiseTables {
+  double inv_c[kLnTab], ln_c[kLnTab];
+  double sn[kScTab], cs[kScTab];
+};
+
+__global__ void noise_tables_kernel(NoiseTables* t) {
+  int i = threadIdx.x;
+  if (i < kLnTab) {
+    double c = 1.0 + (double)(i - 32) / 128.0;  // exact
+    t->inv_c[i] = 1.0 / c;
+    t->ln_c[i] = log(c);
+  }
+  if (i < kScTab) {
+    double sn, cs;
+    sincospi(2.0 * (double)i / kScTab, &sn, &cs);
+    t->sn[i] = sn;
+    t->cs[i] = cs;
+  }
+}
+
+// ln u for u in (0, 1] (normal doubles)
+__device__ __forceinline__ double ln_unit(double u, const NoiseTables& T) {
+  const double LN2 = 0.69314718055994530942;
+  long long b = __double_as_longlong(u);
+  int E = (int)((b >> 52) & 0x7ff) - 1023;
+  double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);  // [1, 2)
+  if (m >= 1.5) {
+    m *= 0.5;  // exact
+    E += 1;
+  }
+  const double d = m - 1.0;                     // exact
+  const int k = 32 + (int)trunc(d * 128.0);     // table cell, c_k = 1 + (k - 32) / 128
+  const double c = 1.0 + (double)(k - 32) * 0.0078125;
+  const double r = (m - c) * T.inv_c[k];        // m - c exact
+  // log1p(r) = r - r^2/2 + r^3/3 - ... + r^9/9
+  double p = fma(r, 1.0 / 9.0, -1.0 / 8.0);
+  p = fma(r, p, 1.0 / 7.0);
+  p = fma(r, p, -1.0 / 6.0);
+  p = fma(r, p, 1.0 / 5.0);
+  p = fma(r, p, -1.0 / 4.0);
+  p = fma(r, p, 1.0 / 3.0);
+  p = fma(r, p, -0.5);
+  p = fma(r * r, p, r);
+  return fma((double)E, LN2, T.ln_c[k] + p);
+}
+
+// (sin, cos) of 2 pi u for u in [0, 1) on the 2^-53 grid
+__device__ __forceinline__ void sincos_2pi(double u, const NoiseTables& T, double& s, double& c) {
+  const double K = 0.024543692606170259675;  // 2 pi / 256
+  double v = u * kScTab;                     // exact
+  double q = floor(v);
+  int iq = (int)q;
+  double x = (v - q) * K;
+  double x2 = x * x;
+  double ps = fma(x2, -1.0 / 5040.0, 1.0 / 120.0);
+  ps = fma(x2, ps, -1.0 / 6.0);
+  double sx = fma(x * x2, ps, x);
+  double pc = fma(x2, 1.0 / 40320.0, -1.0 / 720.0);
+  pc = fma(x2, pc, 1.0 / 24.0);
+  pc = fma(x2, pc, -0.5);
+  double cx = fma(x2, pc, 1.0);
+  double sq = T.sn[iq], cq = T.cs[iq];
+  s = fma(sq, cx, cq * sx);
+  c = fma(cq, cx, -sq * sx);
+}
+
+__global__ void __launch_bounds__(256) lattice_noise_kernel(BlueGeom g, BlueIO io, const NoiseTables* tabs) {
+  __shared__ NoiseTables T;
+  for (int i = threadIdx.x; i < (int)(sizeof(NoiseTables) / sizeof(double)); i += blockDim.x)
+    ((double*)&T)[i] = ((const double*)tabs)[i];
+  __syncthreads();
+  const int l = blockIdx.y, h = blockIdx.z;
+  const int M = g.M[l];
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  U64Pair u = philox_u64(io.noise_seed, kNoiseLattice, (uint32_t)io.noise_t, (uint32_t)j, j == 0 ? 0u : (uint32_t)l,
+                         (uint32_t)(io.noise_rep + h * io.noise_rep_per_rhs));
+  double u1 = ((double)(u.a >> 11) + 1.0) * 0x1.0p-53;
+  double u2 = (double)(u.b >> 11) * 0x1.0p-53;
+  double R = sqrt(fmax(-2.0 * ln_unit(u1, T), 0.0));  // ln 1 may round to a tiny positive value
+  double sn, cs;
+  sincos_2pi(u2, T, sn, cs);
+  cplx* y = io.out + h * io.out_stride + g.off[l] + j;
+  const double sc = io.noise_scale;
+  *y = cadd(*y, cmake(sc * (R * cs), sc * (R * sn)));
+}
+
+static std::mutex g_noise_mu;
+static std::map<int, NoiseTables*> g_noise_tabs;
+
+static const NoiseTables* noise_tables(cudaStream_t s) {
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_noise_mu);
+  auto it = g_noise_tabs.find(dev);
+  if (it != g_noise_tabs.end()) return it->second;
+  NoiseTables* t = nullptr;
+  MR1L_CUDA(cudaMalloc(&t, sizeof(NoiseTables)));
+  MR1L_LAUNCH("noise_tables_kernel", s, 0, (double)sizeof(NoiseTables), noise_tables_kernel<<<1, 256, 0, s>>>(t));
+  MR1L_CUDA(cudaStreamSynchronize(s));
+  g_noise_tabs[dev] = t;
+  return t;
+}
+
+void add_lattice_noise(const BlueGeom& g, const BlueIO& io, int nrhs, cudaStream_t s) {
+  if (io.noise_scale == 0.0 || nrhs == 0) return;
+  int maxM = (int)std::min<int64_t>(g.sum_M, g.P / 2 + 1);
+  dim3 grid(cdiv(maxM, 256), g.L, nrhs);
+  const NoiseTables* tabs = noise_tables(s);
+  MR1L_LAUNCH("lattice_noise_kernel", s, 0, 32.0 * nrhs * g.sum_M, lattice_noise_kernel<<<grid, 256, 0, s>>>(g, io, tabs));
 }
 
 void blue_run(const BlueGeom& g, const BlueIO& io, int mode, int nrhs, cudaStream_t s) {
   int ntrans = g.L * nrhs;
   if (ntrans == 0) return;
-  if (mode == kModeRecon)
-    launch_first_last<kModeRecon>(g, io, ntrans, s);
+  if (mode == kModeRecon) {
+    if (g.df)
+      launch_first_last<kModeRecon, OpsDF>(g, io, ntrans, s);
+    else
+      launch_first_last<kModeRecon, OpsF64>(g, io, ntrans, s);
+    return;
+  }
+  if (g.df)
+    launch_first_last<kModeEval, OpsDF>(g, io, ntrans, s);
   else
-    launch_first_last<kModeEval>(g, io, ntrans, s);
+    launch_first_last<kModeEval, OpsF64>(g, io, ntrans, s);
+  add_lattice_noise(g, io, nrhs, s);
 }
 
 }  // namespace mr1l

@@ -1,5 +1,6 @@
-// Batched prime-length DFTs by Bluestein convolution over power-of-two FP64
-// FFTs (the per-lattice DFT of Algorithm 2 and of the lattice evaluation).
+// Batched prime-length DFTs by Bluestein convolution over FFTs of length 2^k
+// or 3 * 2^k (the per-lattice DFT of Algorithm 2 and of the lattice
+// evaluation), in FP64 or in double-float arithmetic on the FP32 pipes.
 #pragma once
 
 #include "common.cuh"
@@ -27,6 +28,13 @@ struct BlueGeom {
   const cplx* twn;      // device [kSmallTw]: exp(-2 pi i e / n), n = 2^a <= 4096 at offset n,
                         //   n = 3 * 2^a <= 6144 at offset 8192 + n - 3
   int64_t sum_M;        // host: sum of the L lattice sizes (for launch accounting)
+  // double-float arithmetic (df != 0): the same tables as hi/lo FP32 pairs
+  // (float4 = re.hi, re.lo, im.hi, im.lo); Bh then holds float4 data
+  int df;
+  const float4* w_df;
+  const float4* ws_df;
+  const float4* tw_df;
+  const float4* twn_df;
 };
 
 struct BlueIO {
@@ -47,6 +55,11 @@ constexpr int kSmallTw = 8192 + 12288;
 
 // Device-resident twiddle tables, cached per (device, P).
 const cplx* twiddle_table(int P, cudaStream_t s);
+const float4* twiddle_table_df(int P, cudaStream_t s);
+const float4* small_twiddles_df(cudaStream_t s);
+
+// dst[i] = (hi, lo) split of src[i] for i < n (double-float copies of tables).
+void to_double_float(const cplx* src, float4* dst, int64_t n, cudaStream_t s);
 const cplx* small_twiddles(cudaStream_t s);
 
 // The smallest supported convolution length P >= n (2^k <= 2^24 or 3 * 2^k <= 3 * 2^22);
@@ -61,6 +74,10 @@ void blue_filter(const BlueGeom& g, cudaStream_t s);
 
 // Run nrhs * L Bluestein convolutions in mode kModeRecon or kModeEval.
 void blue_run(const BlueGeom& g, const BlueIO& io, int mode, int nrhs, cudaStream_t s);
+
+// y += complex Gaussian noise of every lattice sample (io.out, io.noise_*),
+// using g.L, g.M, g.off and g.sum_M only.
+void add_lattice_noise(const BlueGeom& g, const BlueIO& io, int nrhs, cudaStream_t s);
 
 // Chirp tables w and ws for every lattice (w[n] = exp(-pi i (n^2 mod 2M)/M)).
 void chirp_tables(const BlueGeom& g, int64_t sum_M, cudaStream_t s);
