@@ -271,6 +271,22 @@ def run_reference(args):
 # GPU arm
 # ----------------------------------------------------------------------------
 
+def fast_profile(prof) -> dict:
+    """Kernel shares of the double-float form and the FP64-equivalent rate of
+    its dominant kernel (FFT flops by the 5 n log2 n convention per second)."""
+    if not prof:
+        return {}
+    tot = sum(v["ms"] for v in prof.values()) or 1.0
+    name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    out = {"kernel_share": {k: round(v["ms"] / tot, 4) for k, v in
+                            sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
+    if dom["flops"]:
+        rate = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
+        out["dominant"] = {"kernel": name, "fp64_equivalent_tflops": rate,
+                           "over_fp64_pipe_peak": rate / FP64_PEAK_TFLOPS}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -329,7 +345,7 @@ def run_ours(args):
     bat = timed(True, True)
     clock_info = clocks.stop()
     plain = timed(False, False)
-    fast = None if args.no_fast_fft else timed(True, False, fft="df")
+    fast = None if args.no_fast_fft else timed(True, True, fft="df")
 
     # end to end through the host-buffer API (inputs copied in, results copied out)
     wl.solve(True, host=True)
@@ -412,7 +428,8 @@ def run_ours(args):
             "same_support_as_f64": all(np.array_equal(a.freqs, b.freqs) for a, b in zip(fast["last"], last)),
             "max_rel_coeff_diff_vs_f64": max((float(np.max(np.abs(a.coeffs - b.coeffs) / np.abs(b.coeffs)))
                                              for a, b in zip(fast["last"], last) if b.coeffs.size and
-                                             np.array_equal(a.freqs, b.freqs)), default=None)},
+                                             np.array_equal(a.freqs, b.freqs)), default=None),
+            "gpu_launches": int(fast["launches"]), **fast_profile(fast["prof"])},
         "e2e": {"value": det_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(bat["launches"]),

@@ -249,17 +249,15 @@ struct LatticeWork {
     geom.twn = small_twiddles(s);
     geom.sum_M = sumM;
     geom.df = df;
-    chirp_tables(geom, maxM, s);
     if (df) {
       w_df.reserve(std::max<int64_t>(sumM, 1));
       ws_df.reserve(std::max<int64_t>(sumM, 1));
-      to_double_float(w.get(), w_df.get(), sumM, s);
-      to_double_float(ws.get(), ws_df.get(), sumM, s);
       geom.w_df = w_df.get();
       geom.ws_df = ws_df.get();
       geom.tw_df = twiddle_table_df(P, s);
       geom.twn_df = small_twiddles_df(s);
     }
+    chirp_tables(geom, maxM, s);  // writes the double-float copies as well when df
     blue_filter(geom, s);
   }
 };
@@ -519,9 +517,25 @@ struct SfftRun {
   DevBuf<cplx> line_y, line_bins;
   std::vector<cudaEvent_t> ev;
   std::vector<double> final_coeffs;
+  // measurement noise: drawn on a side stream while the main stream runs the
+  // sampler's inverse transform (FP64 noise work overlaps the FFT work), then
+  // added to the samples by the reconstruct pass as it loads them
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_free = nullptr, ev_noise = nullptr;
+  DevBuf<cplx> noise;
 
   ~SfftRun() {
     for (auto e : ev) cudaEventDestroy(e);
+    if (ev_free) cudaEventDestroy(ev_free);
+    if (ev_noise) cudaEventDestroy(ev_noise);
+    if (side) cudaStreamDestroy(side);
+  }
+
+  void noise_setup() {
+    if (side) return;
+    MR1L_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    MR1L_CUDA(cudaEventCreateWithFlags(&ev_free, cudaEventDisableTiming));
+    MR1L_CUDA(cudaEventCreateWithFlags(&ev_noise, cudaEventDisableTiming));
   }
 
   void ev_record() {
@@ -606,6 +620,26 @@ struct SfftRun {
         if (rc != 0) throw Error(MR1L_E_SAMPLER, "sampler callback failed (lattice request)");
       }
     } else {
+      const bool noisy = S.sigma > 0;
+      if (noisy) {
+        // the previous pass has consumed the noise buffer once the main stream
+        // reaches this point; draw this pass's noise on the side stream
+        noise_setup();
+        noise.reserve((size_t)nrep * sumM);
+        MR1L_CUDA(cudaEventRecord(ev_free, s));
+        MR1L_CUDA(cudaStreamWaitEvent(side, ev_free, 0));
+        BlueIO nio{};
+        nio.out = noise.get();
+        nio.out_stride = sumM;
+        nio.noise_scale = S.sigma / std::sqrt(2.0);
+        nio.noise_write = 1;
+        nio.noise_seed = S.noise_seed;
+        nio.noise_t = t;
+        nio.noise_rep = rep0;
+        nio.noise_rep_per_rhs = 1;
+        add_lattice_noise(lw.geom, nio, nrep, side);
+        MR1L_CUDA(cudaEventRecord(ev_noise, side));
+      }
       bins.reserve((size_t)nrep * sumM);
       MR1L_CUDA(cudaMemsetAsync(bins.get(), 0, (size_t)nrep * sumM * sizeof(cplx), s));
       planted_lattice_bins(freqs_ptr, coeffs_ptr, S.s, P.d, t, anchors.get(), nrep, lw.dev(), lw.Luse, lw.geom,
@@ -616,17 +650,14 @@ struct SfftRun {
       io.out = y.get();
       io.out_stride = sumM;
       io.work = work.get();
-      io.noise_scale = S.sigma > 0 ? S.sigma / std::sqrt(2.0) : 0.0;
-      io.noise_seed = S.noise_seed;
-      io.noise_t = t;
-      io.noise_rep = rep0;
-      io.noise_rep_per_rhs = 1;
       blue_run(lw.geom, io, kModeEval, nrep, s);
+      if (noisy) MR1L_CUDA(cudaStreamWaitEvent(s, ev_noise, 0));
     }
     ev_record();
     BlueIO io{};
     io.in = y.get();
     io.in_stride = sumM;
+    io.add_in = (!S.fn && S.sigma > 0) ? noise.get() : nullptr;
     io.out = C.get();
     io.out_stride = sumM;
     io.work = work.get();

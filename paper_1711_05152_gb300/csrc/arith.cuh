@@ -26,10 +26,13 @@ struct OpsF64 {
   static __device__ __forceinline__ V conj(V a) { return cconj(a); }
   template <bool INV>
   static __device__ __forceinline__ V mi(V a) { return mul_mi<INV>(a); }
-  // a * s for a real constant given as double
+  // a * s for a real s given as double (FP64) or as the FP32 pair hi + lo
   static __device__ __forceinline__ V scale(V a, double s) { return cmake(a.x * s, a.y * s); }
+  static __device__ __forceinline__ V scalec(V a, double s, float, float) { return cmake(a.x * s, a.y * s); }
+  static __device__ __forceinline__ V half(V a) { return cmake(0.5 * a.x, 0.5 * a.y); }
   static __device__ __forceinline__ V from(cplx a) { return a; }
   static __device__ __forceinline__ cplx to(V a) { return a; }
+  static __device__ __forceinline__ bool nonzero(V a) { return a.x != 0.0 || a.y != 0.0; }
 };
 
 // ---------------------------------------------------------------------------
@@ -112,13 +115,21 @@ struct OpsDF {
   static __device__ __forceinline__ V mi(V a) {
     return INV ? make_float4(-a.z, -a.w, a.x, a.y) : make_float4(a.z, a.w, -a.x, -a.y);
   }
+  // a * s, s split on the fly (FP64 work: keep out of inner loops)
   static __device__ __forceinline__ V scale(V a, double s) {
     float sh = __double2float_rn(s);
     float sl = __double2float_rn(s - (double)sh);
+    return scalec(a, s, sh, sl);
+  }
+  // a * (sh + sl) for a constant given as its FP32 pair
+  static __device__ __forceinline__ V scalec(V a, double, float sh, float sl) {
     V r;
     dw_mul(a.x, a.y, sh, sl, r.x, r.y);
     dw_mul(a.z, a.w, sh, sl, r.z, r.w);
     return r;
+  }
+  static __device__ __forceinline__ V half(V a) {  // exact
+    return make_float4(0.5f * a.x, 0.5f * a.y, 0.5f * a.z, 0.5f * a.w);
   }
   static __device__ __forceinline__ V from(cplx a) {
     float rh = __double2float_rn(a.x), ih = __double2float_rn(a.y);
@@ -127,6 +138,7 @@ struct OpsDF {
   static __device__ __forceinline__ cplx to(V a) {
     return cmake((double)a.x + (double)a.y, (double)a.z + (double)a.w);
   }
+  static __device__ __forceinline__ bool nonzero(V a) { return a.x != 0.f || a.z != 0.f; }
 };
 
 }  // namespace mr1l

@@ -65,14 +65,19 @@ struct RegDft<4, INV, O> {
   }
 };
 
+// 1/sqrt(2) and sqrt(3)/2 as FP64 and as FP32 pairs hi + lo (hi = the FP32
+// rounding, lo = the FP32 rounding of the remainder)
+#define MR1L_INV_SQRT2 0.70710678118654752440, 0x1.6a09e6p-1f, 0x1.9fcef4p-27f
+#define MR1L_SQRT3_2 0.86602540378443864676, 0x1.bb67aep-1f, 0x1.0b0996p-26f
+
 // w8 = exp(-+ 2 pi i / 8): w8 x = (x + mi(x)) / sqrt2, w8^3 x = (mi(x) - x) / sqrt2
 template <bool INV, class O>
 __device__ __forceinline__ typename O::V w8_1(typename O::V x) {
-  return O::scale(O::add(x, O::template mi<INV>(x)), 0.70710678118654752440);
+  return O::scalec(O::add(x, O::template mi<INV>(x)), MR1L_INV_SQRT2);
 }
 template <bool INV, class O>
 __device__ __forceinline__ typename O::V w8_3(typename O::V x) {
-  return O::scale(O::sub(O::template mi<INV>(x), x), 0.70710678118654752440);
+  return O::scalec(O::sub(O::template mi<INV>(x), x), MR1L_INV_SQRT2);
 }
 
 template <bool INV, class O>
@@ -105,8 +110,8 @@ struct RegDft<3, INV, O> {
     V t1 = O::add(v[1], v[2]), t2 = O::sub(v[1], v[2]);
     V a = v[0];
     v[0] = O::add(a, t1);
-    V m1 = O::sub(a, O::scale(t1, 0.5));
-    V m2 = O::scale(O::template mi<INV>(t2), 0.86602540378443864676);
+    V m1 = O::sub(a, O::half(t1));
+    V m2 = O::scalec(O::template mi<INV>(t2), MR1L_SQRT3_2);
     v[1] = O::add(m1, m2);
     v[2] = O::sub(m1, m2);
   }
@@ -272,20 +277,11 @@ __device__ __forceinline__ typename O::V load_input(const BlueGeom& g, const Blu
     return O::zero();
   }
   if (n >= M) return O::zero();
-  typename O::V x = O::from(io.in[h * io.in_stride + off + n]);
+  cplx y = io.in[h * io.in_stride + off + n];
+  if (MODE == kModeRecon && io.add_in) y = cadd(y, io.add_in[h * io.in_stride + off + n]);
+  typename O::V x = O::from(y);
   if (MODE == kModeRecon) return O::mul(x, Tab<O>::ws(g)[off + n]);
   return O::mul(O::conj(x), Tab<O>::w(g)[off + n]);
-}
-
-__device__ __forceinline__ cplx lattice_noise(uint64_t seed, int t, int rep, int l, int64_t j, double scale) {
-  U64Pair u = philox_u64(seed, kNoiseLattice, (uint32_t)t, (uint32_t)j, j == 0 ? 0u : (uint32_t)l,
-                         (uint32_t)rep);
-  double u1 = ((double)(u.a >> 11) + 1.0) * 0x1.0p-53;
-  double u2 = (double)(u.b >> 11) * 0x1.0p-53;
-  double R = sqrt(-2.0 * log(u1));
-  double sn, cs;
-  sincospi(2.0 * u2, &sn, &cs);
-  return cmake(scale * (R * cs), scale * (R * sn));
 }
 
 template <int MODE, class O>
@@ -322,7 +318,8 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
   V* Bh = Tab<O>::Bh(g) + (int64_t)l * P;
   if (MODE == kModeFilter) {
     const double sc = 1.0 / (double)P;
-    for (int n = threadIdx.x; n < P; n += blockDim.x) Bh[n] = O::scale(sm[n], sc);
+    const float sh = __double2float_rn(sc), sl = __double2float_rn(sc - (double)sh);
+    for (int n = threadIdx.x; n < P; n += blockDim.x) Bh[n] = O::scalec(sm[n], sc, sh, sl);
     return;
   }
   for (int n = threadIdx.x; n < P; n += blockDim.x) sm[n] = O::mul(sm[n], Bh[n]);
@@ -365,21 +362,61 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
   const int n2_0 = blockIdx.x * CB;
   // RECON / EVAL: rows n1 >= P1/2 hold n >= P/2 >= M, i.e. zero padding
   const int rows = MODE == kModeFilter ? P1 : P1 / 2;
-  for (int e = threadIdx.x; e < rows * CB; e += blockDim.x) {
-    int i = e / CB, b = e - i * CB;
-    sm[e] = load_input<MODE, O>(g, io, h, M, off, (int64_t)i * P2 + n2_0 + b);
+  V* work = (V*)io.work + (int64_t)gi * P;
+  // 4-step twiddle w_P^(n2 k1): n2 < P2 and k1 < P1, so n2 k1 < P indexes the
+  // table without reduction
+  const V* tw = Tab<O>::tw(g);
+  if (MODE == kModeEval) {
+    // Evaluation inputs are often sparse (the bins of a few planted
+    // frequencies).  Columns with at most kColNz non-zeros are transformed as
+    // direct sums X[k1] = sum_nz x[n1] w_P1^(n1 k1), cheaper than the FFT.
+    constexpr int kColNz = 8;
+    __shared__ int nzc[16];
+    __shared__ short nzi[16][kColNz];
+    __shared__ int over;
+    if (threadIdx.x < 16) nzc[threadIdx.x] = 0;
+    if (threadIdx.x == 0) over = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * CB; e += blockDim.x) {
+      int i = e / CB, b = e - i * CB;
+      V x = load_input<MODE, O>(g, io, h, M, off, (int64_t)i * P2 + n2_0 + b);
+      sm[e] = x;
+      if (O::nonzero(x)) {
+        int slot = atomicAdd(&nzc[b], 1);
+        if (slot < kColNz) nzi[b][slot] = (short)i;
+        else over = 1;
+      }
+    }
+    __syncthreads();
+    if (!over) {
+      const V* twP1 = twiddles_of(Tab<O>::twn(g), P1);
+      for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
+        int k1 = e / CB, b = e - k1 * CB;
+        V acc = O::zero();
+        for (int q = 0; q < nzc[b]; ++q) {
+          int n1 = nzi[b][q];
+          acc = O::add(acc, O::mul(sm[n1 * CB + b], twP1[(n1 * k1) % P1]));
+        }
+        int n2 = n2_0 + b;
+        work[(int64_t)k1 * P2 + n2] = O::mul(acc, tw[n2 * k1]);
+      }
+      return;
+    }
+  } else {
+    for (int e = threadIdx.x; e < rows * CB; e += blockDim.x) {
+      int i = e / CB, b = e - i * CB;
+      sm[e] = load_input<MODE, O>(g, io, h, M, off, (int64_t)i * P2 + n2_0 + b);
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (MODE == kModeFilter)
     smem_fft<false, true, O>(sm, P1, CB, 1, CB, Tab<O>::twn(g));
   else
     smem_fft<false, true, O, true>(sm, P1, CB, 1, CB, Tab<O>::twn(g));
-  V* work = (V*)io.work + (int64_t)gi * P;
-  const V* tw = Tab<O>::tw(g);
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int k1 = e / CB, b = e - k1 * CB;
     int n2 = n2_0 + b;
-    work[(int64_t)k1 * P2 + n2] = O::mul(sm[e], tw[((int64_t)n2 * k1) % P]);
+    work[(int64_t)k1 * P2 + n2] = O::mul(sm[e], tw[n2 * k1]);
   }
 }
 
@@ -401,7 +438,8 @@ __global__ void __launch_bounds__(512) blue_row_kernel(BlueGeom g, BlueIO io) {
   V* Bh = Tab<O>::Bh(g) + (int64_t)l * P + (int64_t)k1_0 * P2;
   if (FILTER) {
     const double sc = 1.0 / (double)P;
-    for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) Bh[e] = O::scale(sm[e], sc);
+    const float sh = __double2float_rn(sc), sl = __double2float_rn(sc - (double)sh);
+    for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) Bh[e] = O::scalec(sm[e], sc, sh, sl);
     return;
   }
   for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = O::mul(sm[e], Bh[e]);
@@ -411,7 +449,7 @@ __global__ void __launch_bounds__(512) blue_row_kernel(BlueGeom g, BlueIO io) {
   for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) {
     int b = e / P2, n2 = e - b * P2;
     int k1 = k1_0 + b;
-    work[e] = O::mulc(sm[e], tw[((int64_t)n2 * k1) % P]);
+    work[e] = O::mulc(sm[e], tw[n2 * k1]);
   }
 }
 
@@ -470,7 +508,8 @@ __global__ void small_twiddle_kernel(cplx* tw) {
   tw[i] = cmake(cs, -sn);
 }
 
-__global__ void chirp_kernel(cplx* w, cplx* ws, const int64_t* off, const int* Ms, int L) {
+__global__ void chirp_kernel(cplx* w, cplx* ws, float4* w_df, float4* ws_df, const int64_t* off, const int* Ms,
+                             int L) {
   int l = blockIdx.y;
   int M = Ms[l];
   int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -479,9 +518,14 @@ __global__ void chirp_kernel(cplx* w, cplx* ws, const int64_t* off, const int* M
   double s, c;
   sincospi((double)q / (double)M, &s, &c);
   cplx v = cmake(c, -s);  // exp(-pi i q / M)
-  w[off[l] + n] = v;
   double inv = 1.0 / (double)M;
-  ws[off[l] + n] = cmake(c * inv, -s * inv);
+  cplx vs = cmake(c * inv, -s * inv);
+  w[off[l] + n] = v;
+  ws[off[l] + n] = vs;
+  if (w_df) {  // double-float copies for the double-float passes
+    w_df[off[l] + n] = OpsDF::from(v);
+    ws_df[off[l] + n] = OpsDF::from(vs);
+  }
 }
 
 namespace {
@@ -599,12 +643,15 @@ void blue_split(BlueGeom& g, int P) {
 void chirp_tables(const BlueGeom& g, int64_t max_M, cudaStream_t s) {
   dim3 grid(cdiv(max_M, 256), g.L);
   MR1L_LAUNCH("chirp_kernel", s, 0, 32.0 * g.sum_M,
-              chirp_kernel<<<grid, 256, 0, s>>>(const_cast<cplx*>(g.w), const_cast<cplx*>(g.ws), g.off, g.M, g.L));
+              chirp_kernel<<<grid, 256, 0, s>>>(const_cast<cplx*>(g.w), const_cast<cplx*>(g.ws), const_cast<float4*>(g.w_df),
+                                    const_cast<float4*>(g.ws_df), g.off, g.M, g.L));
 }
 
 template <typename K>
 static void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) MR1L_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  // the 48 KB default bounds static + dynamic shared memory together, and the
+  // column kernels hold a few hundred bytes of static shared memory
+  if (bytes > 32 * 1024) MR1L_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
 static int threads_for(int elems) {
@@ -774,7 +821,8 @@ __global__ void __launch_bounds__(256) lattice_noise_kernel(BlueGeom g, BlueIO i
   sincos_2pi(u2, T, sn, cs);
   cplx* y = io.out + h * io.out_stride + g.off[l] + j;
   const double sc = io.noise_scale;
-  *y = cadd(*y, cmake(sc * (R * cs), sc * (R * sn)));
+  const cplx e = cmake(sc * (R * cs), sc * (R * sn));
+  *y = io.noise_write ? e : cadd(*y, e);
 }
 
 static std::mutex g_noise_mu;

@@ -43,8 +43,12 @@ struct BlueIO {
   cplx* out;            // RECON: C; EVAL: y
   int64_t out_stride;
   cplx* work;           // [nrhs][L][P]
-  // optional complex Gaussian noise added in EVAL mode (Philox purpose 5)
+  // RECON: optional second input added to the samples as they are loaded
+  // (the measurement noise, computed concurrently on another stream)
+  const cplx* add_in;   // [nrhs][sum M] with stride in_stride, or null
+  // complex Gaussian noise (Philox purpose 5) written by add_lattice_noise
   double noise_scale;   // sigma / sqrt(2); 0 disables
+  int noise_write;      // 1: out = noise; 0: out += noise
   uint64_t noise_seed;
   int noise_t, noise_rep;
   int noise_rep_per_rhs;  // rep index = noise_rep + rhs * noise_rep_per_rhs

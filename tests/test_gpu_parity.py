@@ -136,6 +136,23 @@ def test_large_single_lattice_4step(M):
     assert _normwise(yb[0] if yb.ndim > 1 else yb, wantb) < RTOL
 
 
+@pytest.mark.parametrize("M", [1_300_021, 2_000_003])
+@pytest.mark.parametrize("width", [300, 30000])
+def test_large_lattice_evaluation(M, width):
+    """Lattice evaluation through the 4-step passes, with Bluestein lengths
+    3 * 2^20 and 3 * 2^21 (a 48 KB column tile): few candidates leave every
+    column of the padded input with a handful of non-zeros (the direct column
+    transform), many leave dozens per column (the column FFT)."""
+    I = np.arange(-width, width).reshape(-1, 1)
+    pl = P.plan(I, [M], [[7919]])
+    ml = lattice.MultiLattice([M], [np.array([7919])], [lattice.unique_mask(I, [7919], M)], True, 1)
+    rng = np.random.default_rng(M + width)
+    c = rng.standard_normal(I.shape[0]) + 1j * rng.standard_normal(I.shape[0])
+    got = pl.evaluate(torch.from_numpy(c).cuda(), P.MR1L_EVAL).cpu().numpy()
+    want = np.concatenate(lattice.evaluate(I, ml, c, "eval", "fft"))
+    assert _normwise(got[0] if got.ndim > 1 else got, want) < RTOL
+
+
 def _sfft_pair(name, seed, batch=False):
     sig, p = W.workload(name, seed)
     out = P.sfft_dimincr(sig.d, sig.N, p["s"], p["r"], p["theta"], p["theta_mode"], seed=seed, b=p["b"],
