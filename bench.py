@@ -439,6 +439,7 @@ def run_ours(args):
                               "note": "Algorithm 2 passes (Bluestein + gather), algorithmic bytes "
                                       "16*sum_M + 24*|J| per pass; FP64-bound, see roofline"},
         "kernel_share": kernel_share,
+        "tile_tuner": tile_summary(P.tune_read()),
         "clocks": clock_info,
         "cpu_baseline": cpu,
         "detected": int(sum(o.freqs.shape[0] for o in last)), "support_exact": wl.exact(last),
@@ -447,6 +448,94 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def tile_summary(table):
+    """Column/row tile chosen per Bluestein length, mode and arithmetic
+    ("P/mode[/df]": [col_tile, row_tile]) by the library's tile tuner."""
+    return {f"{e['P']}/{e['mode']}{'/df' if e['df'] else ''}": [e["col_tile"], e["row_tile"]]
+            for e in sorted(table, key=lambda e: (e["df"], e["P"], e["mode"]))}
+
+
+# ---------------------------------------------------------------------------
+# The paper's statistical experiments (Tables 5.1, 5.2, 5.4) on the GPU path
+# ---------------------------------------------------------------------------
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def _paper_rows(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.strip() and not line.startswith("#"):
+            rows.append([float(x) for x in line.split()])
+    return rows
+
+
+def _run_stats(problems, sigs, fft):
+    """Detected-set and coefficient statistics of a list of planted problems."""
+    import paper_1711_05152_gb300 as P
+    for q in problems:
+        q["fft"] = fft
+    outs = P.sfft_dimincr_batch(problems, concurrency=16)
+    samples, correct, success, err = [], [], [], []
+    for sig, o in zip(sigs, outs):
+        truth = {tuple(f): c for f, c in zip(sig.freqs.astype(int).tolist(), sig.coeffs)}
+        got = {tuple(f): c for f, c in zip(o.freqs.tolist(), o.coeffs)}
+        keys = set(truth) | set(got)
+        num = sum(abs(got.get(k, 0.0) - truth.get(k, 0.0)) ** 2 for k in keys)
+        samples.append(o.samples)
+        correct.append(len(set(truth) & set(got)))
+        success.append(set(truth) == set(got))
+        err.append(float(np.sqrt(num / sum(abs(c) ** 2 for c in truth.values()))))
+    return {"max_samples": int(max(samples)), "min_correct": int(min(correct)),
+            "success_rate": float(np.mean(success)), "max_rel_l2": float(max(err))}
+
+
+def run_paper_table(args):
+    """One JSON line per row of the paper's Table 5.1 (samples and errors,
+    Section 5.1), 5.2 (success rates over r and the absolute threshold) or
+    5.4 (noise, Section 5.2), measured on the GPU path with the paper's
+    protocol and seeded synthetic signals, beside the paper's printed values
+    (tests/golden/paper_table_*.txt)."""
+    reps, base = args.reps, 1000 * args.seed
+    if args.paper_table == "5.1":
+        sizes = {int(x) for x in args.sizes.split(",")}
+        for d, supp, pmax, perr in _paper_rows("paper_table_5_1.txt"):
+            d, supp = int(d), int(supp)
+            if supp not in sizes:
+                continue
+            t0 = time.time()
+            sigs = [W.planted_signal(d, 32, supp, seed=base + i, model="box") for i in range(reps)]
+            probs = [dict(d=d, N=32, s=supp, s_local=supp, r=1, b=10, theta=1e-12, theta_mode="abs",
+                          seed=base + i, freqs=g.freqs, coeffs=g.coeffs) for i, g in enumerate(sigs)]
+            st = _run_stats(probs, sigs, args.fft)
+            print(json.dumps({"paper_table": "5.1", "d": d, "supp": supp, "reps": reps, "fft": args.fft, **st,
+                              "paper": {"max_samples": int(pmax), "max_rel_l2": perr},
+                              "samples_over_paper": st["max_samples"] / pmax,
+                              "seconds": round(time.time() - t0, 2)}), flush=True)
+    elif args.paper_table == "5.2":
+        for r, delta, pmin, prate in _paper_rows("paper_table_5_2.txt"):
+            t0 = time.time()
+            sigs = [W.planted_signal(5, 32, 1000, seed=base + i, model="unimodular") for i in range(reps)]
+            probs = [dict(d=5, N=32, s=1000, s_local=1000, r=int(r), b=10, theta=delta, theta_mode="abs",
+                          seed=base + i, freqs=g.freqs, coeffs=g.coeffs) for i, g in enumerate(sigs)]
+            st = _run_stats(probs, sigs, args.fft)
+            print(json.dumps({"paper_table": "5.2", "r": int(r), "delta": delta, "reps": reps, "fft": args.fft,
+                              **st, "paper": {"min_correct": int(pmin), "success_rate": prate, "reps": 1000},
+                              "seconds": round(time.time() - t0, 2)}), flush=True)
+    else:
+        for snr, r, pmax, pmin, prate, perr in _paper_rows("paper_table_5_4.txt"):
+            t0 = time.time()
+            sigs = [W.planted_signal(10, 32, 1000, seed=base + i, model="unimodular", snr_db=snr)
+                    for i in range(reps)]
+            probs = [dict(d=10, N=32, s=1000, s_local=1000, r=int(r), b=10, theta=1e-12, theta_mode="abs",
+                          seed=base + i, freqs=g.freqs, coeffs=g.coeffs, sigma=g.sigma) for i, g in enumerate(sigs)]
+            st = _run_stats(probs, sigs, args.fft)
+            print(json.dumps({"paper_table": "5.4", "snr_db": int(snr), "r": int(r), "reps": reps, "fft": args.fft,
+                              **st, "paper": {"max_samples": int(pmax), "min_correct": int(pmin),
+                                              "success_rate": prate, "max_rel_l2": perr, "reps": 1000},
+                              "seconds": round(time.time() - t0, 2)}), flush=True)
     return 0
 
 
@@ -482,12 +571,18 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIPTIONS),
                     help="plain_d10 (default line), large_d25 or batch256")
     ap.add_argument("--no-fast-fft", action="store_true", help="skip the double-float FFT form")
-    ap.add_argument("--fft", default="f64", choices=["f64", "df"], help="arithmetic of --kernel-case")
+    ap.add_argument("--fft", default="f64", choices=["f64", "df"], help="arithmetic of --kernel-case and --paper-table")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the lattice transform at the workload size (for ncu captures)")
+    ap.add_argument("--paper-table", choices=["5.1", "5.2", "5.4"],
+                    help="rerun one of the paper's statistical experiments on the GPU path")
+    ap.add_argument("--reps", type=int, default=10, help="repetitions per row of --paper-table")
+    ap.add_argument("--sizes", default="1000,10000", help="sparsities of the --paper-table 5.1 rows")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
+    if args.paper_table:
+        return run_paper_table(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

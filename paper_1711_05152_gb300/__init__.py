@@ -43,6 +43,7 @@ EXPORTS = [
     "mr1l_last_error", "mr1l_version", "mr1l_plan", "mr1l_plan_search", "mr1l_plan_info",
     "mr1l_plan_masks", "mr1l_destroy", "mr1l_reconstruct", "mr1l_evaluate", "sfft_dimincr",
     "sfft_free", "sfft_dimincr_batch", "mr1l_reconstruct_noalloc", "mr1l_lattice_noise", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
+    "mr1l_tune_enable", "mr1l_tune_reset", "mr1l_tune_read",
 ]
 
 
@@ -125,6 +126,9 @@ def lib() -> C.CDLL:
     L.mr1l_prof_launches.argtypes = []
     L.mr1l_prof_launches.restype = C.c_longlong
     L.mr1l_prof_read.argtypes = [C.c_char_p, C.c_size_t]
+    L.mr1l_tune_enable.argtypes = [C.c_int]
+    L.mr1l_tune_reset.argtypes = []
+    L.mr1l_tune_read.argtypes = [C.c_char_p, C.c_size_t]
     _lib = L
     return L
 
@@ -419,4 +423,22 @@ def prof_read() -> dict:
     import json
     buf = C.create_string_buffer(1 << 16)
     _check(lib().mr1l_prof_read(buf, 1 << 16))
+    return json.loads(buf.value.decode())
+
+
+def tune_enable(on: bool = True) -> None:
+    """Allow (or forbid) the tiling trials of the tile tuner (see mr1l_tune_enable)."""
+    _check(lib().mr1l_tune_enable(1 if on else 0))
+
+
+def tune_reset() -> None:
+    """Forget every cached tile choice."""
+    _check(lib().mr1l_tune_reset())
+
+
+def tune_read() -> list:
+    """The cached tile choices [{device, P, mode, df, col_tile, row_tile, col_ms, row_ms}, ...]."""
+    import json
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().mr1l_tune_read(buf, 1 << 16))
     return json.loads(buf.value.decode())

@@ -960,6 +960,7 @@ extern "C" int mr1l_reconstruct_noalloc(mr1l_plan_t* plan, const void* y, int nr
     io.out = Cbuf;
     io.out_stride = sumM;
     io.work = work;
+    io.no_tune = 1;  // tiling trials would synchronise and create events
     blue_run(lw.geom, io, kModeRecon, nrhs, s);
     gather(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, Cbuf, sumM, nrhs, (cplx*)c, plan->nI,
            nullptr, nullptr, s);
@@ -1005,5 +1006,25 @@ extern "C" int mr1l_lattice_noise(uint64_t seed, int t, int rep, int L, const in
     io.noise_rep_per_rhs = 1;
     add_lattice_noise(g, io, 1, s);
     MR1L_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Tile tuner control
+// ---------------------------------------------------------------------------
+extern "C" int mr1l_tune_enable(int on) {
+  return guarded([&] { tune_enable(on); });
+}
+
+extern "C" int mr1l_tune_reset(void) {
+  return guarded([&] { tune_reset(); });
+}
+
+extern "C" int mr1l_tune_read(char* buf, size_t len) {
+  return guarded([&] {
+    const std::string js = tune_json();
+    if (!buf || len < js.size() + 1)
+      throw Error(MR1L_E_INVAL, "buffer too small for the tile table (" + std::to_string(js.size() + 1) + " bytes)");
+    std::memcpy(buf, js.c_str(), js.size() + 1);
   });
 }

@@ -22,10 +22,15 @@
 //   pass 3 (columns): inverse FFT_P1 over k1, natural order x[n1 P2 + n2].
 // Each sub-FFT is a mixed-radix (8, 4, 2, 3) Stockham autosort FFT in shared
 // memory (Govindaraju et al., SC'08 formulation).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <type_traits>
+#include <vector>
 
 #include <cmath>
 
@@ -331,21 +336,27 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
 // ---------------------------------------------------------------------------
 // 4-step passes
 // ---------------------------------------------------------------------------
-// Tiles of 2048 complex (32 KB shared memory, 256 threads) so that three CTAs
-// share an SM and hide each other's load and barrier phases; a single
-// column or row of more than 2048 takes a tile of its own length.
+// A CTA transforms a tile of `tile` complex elements (tile / 8 threads): CB
+// columns of length P1 or RB rows of length P2, CB and RB powers of two (so
+// they divide P2 and P1); a single column or row longer than the tile takes a
+// tile of its own length.  The tile size is picked per (P, mode, arithmetic)
+// by the tile tuner below from kTileCands; 2048 (32 KB of shared memory,
+// 256 threads, three CTAs per SM) is the default.
 constexpr int kTileElems = 2048;
-__host__ __device__ __forceinline__ int col_tile(int P1) {
-  int cb = kTileElems / P1;  // P1 = 3 * 2^a gives a tile of 3/4 x 2048
+constexpr int kTileCands[3] = {1024, 2048, 4096};
+__host__ __device__ __forceinline__ int col_tile(int P1, int tile) {
+  int cb = tile / P1;  // P1 = 3 * 2^a gives a tile of 3/4 x tile
   if (cb > 16) cb = 16;
   if (cb < 1) cb = 1;
-  int p = 1;  // power of two, so it divides P2
+  int p = 1;
   while (2 * p <= cb) p *= 2;
   return p;
 }
-__host__ __device__ __forceinline__ int row_tile(int P2) {
-  int rb = kTileElems / P2;
-  return rb < 1 ? 1 : rb;
+__host__ __device__ __forceinline__ int row_tile(int P2, int P1, int tile) {
+  int rb = tile / P2;
+  int p = 1;  // power of two dividing P1 (= 2^a or 3 * 2^a)
+  while (2 * p <= rb && P1 % (2 * p) == 0) p *= 2;
+  return p;
 }
 
 // Pass 1: columns, forward, with the 4-step twiddle.
@@ -356,7 +367,7 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
   V* sm = (V*)smraw;
   const int gi = blockIdx.y;
   const int l = gi % g.L, h = gi / g.L;
-  const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1);
+  const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1, g.ctile);
   const int M = g.M[l];
   const int64_t off = g.off[l];
   const int n2_0 = blockIdx.x * CB;
@@ -366,14 +377,24 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
   // 4-step twiddle w_P^(n2 k1): n2 < P2 and k1 < P1, so n2 k1 < P indexes the
   // table without reduction
   const V* tw = Tab<O>::tw(g);
+  // Evaluation inputs are often sparse (the bins of a few planted
+  // frequencies).  A column with at most kColNz non-zeros is transformed as
+  // the direct sum X[k1] = sum_nz x[n1] w_P1^(n1 k1) over its non-zeros in
+  // ascending n1, whatever the tiling; the column FFT runs only when some
+  // column of the tile has more.  So every column gets the same arithmetic
+  // under every tile size.
+  constexpr int kColNz = 8;
+  __shared__ int nzc[16];
+  __shared__ short nzi[16][kColNz];
+  __shared__ V nzv[16][kColNz];
+  __shared__ int over;
+  const V* twP1 = twiddles_of(Tab<O>::twn(g), P1);
+  auto direct = [&](int b, int k1) {
+    V acc = O::zero();
+    for (int q = 0; q < nzc[b]; ++q) acc = O::add(acc, O::mul(nzv[b][q], twP1[(nzi[b][q] * k1) % P1]));
+    return acc;
+  };
   if (MODE == kModeEval) {
-    // Evaluation inputs are often sparse (the bins of a few planted
-    // frequencies).  Columns with at most kColNz non-zeros are transformed as
-    // direct sums X[k1] = sum_nz x[n1] w_P1^(n1 k1), cheaper than the FFT.
-    constexpr int kColNz = 8;
-    __shared__ int nzc[16];
-    __shared__ short nzi[16][kColNz];
-    __shared__ int over;
     if (threadIdx.x < 16) nzc[threadIdx.x] = 0;
     if (threadIdx.x == 0) over = 0;
     __syncthreads();
@@ -383,22 +404,35 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
       sm[e] = x;
       if (O::nonzero(x)) {
         int slot = atomicAdd(&nzc[b], 1);
-        if (slot < kColNz) nzi[b][slot] = (short)i;
-        else over = 1;
+        if (slot < kColNz) {
+          nzi[b][slot] = (short)i;
+          nzv[b][slot] = x;
+        } else {
+          over = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < CB && nzc[threadIdx.x] <= kColNz) {  // slots in ascending n1
+      const int b = threadIdx.x;
+      for (int q = 1; q < nzc[b]; ++q) {
+        const short iq = nzi[b][q];
+        const V vq = nzv[b][q];
+        int r = q;
+        for (; r > 0 && nzi[b][r - 1] > iq; --r) {
+          nzi[b][r] = nzi[b][r - 1];
+          nzv[b][r] = nzv[b][r - 1];
+        }
+        nzi[b][r] = iq;
+        nzv[b][r] = vq;
       }
     }
     __syncthreads();
     if (!over) {
-      const V* twP1 = twiddles_of(Tab<O>::twn(g), P1);
       for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
         int k1 = e / CB, b = e - k1 * CB;
-        V acc = O::zero();
-        for (int q = 0; q < nzc[b]; ++q) {
-          int n1 = nzi[b][q];
-          acc = O::add(acc, O::mul(sm[n1 * CB + b], twP1[(n1 * k1) % P1]));
-        }
         int n2 = n2_0 + b;
-        work[(int64_t)k1 * P2 + n2] = O::mul(acc, tw[n2 * k1]);
+        work[(int64_t)k1 * P2 + n2] = O::mul(direct(b, k1), tw[n2 * k1]);
       }
       return;
     }
@@ -416,7 +450,9 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int k1 = e / CB, b = e - k1 * CB;
     int n2 = n2_0 + b;
-    work[(int64_t)k1 * P2 + n2] = O::mul(sm[e], tw[n2 * k1]);
+    V v = sm[e];
+    if (MODE == kModeEval && nzc[b] <= kColNz) v = direct(b, k1);
+    work[(int64_t)k1 * P2 + n2] = O::mul(v, tw[n2 * k1]);
   }
 }
 
@@ -429,7 +465,7 @@ __global__ void __launch_bounds__(512) blue_row_kernel(BlueGeom g, BlueIO io) {
   V* sm = (V*)smraw;
   const int gi = blockIdx.y;
   const int l = gi % g.L;
-  const int P = g.P, P2 = g.P2, RB = row_tile(P2);
+  const int P = g.P, P2 = g.P2, RB = row_tile(P2, g.P1, g.rtile);
   const int k1_0 = blockIdx.x * RB;
   V* work = (V*)io.work + (int64_t)gi * P + (int64_t)k1_0 * P2;
   for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = work[e];
@@ -461,7 +497,7 @@ __global__ void __launch_bounds__(512) blue_col_inv_kernel(BlueGeom g, BlueIO io
   V* sm = (V*)smraw;
   const int gi = blockIdx.y;
   const int l = gi % g.L, h = gi / g.L;
-  const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1);
+  const int P = g.P, P1 = g.P1, P2 = g.P2, CB = col_tile(P1, g.ctile);
   const int M = g.M[l];
   const int64_t off = g.off[l];
   const int n2_0 = blockIdx.x * CB;
@@ -665,46 +701,190 @@ static double fft_flops(double n) { return n > 1 ? 5.0 * n * std::log2(n) : 0.0;
 // Algorithmic work of one launch (FFT flops by the 5 n log2 n convention plus
 // 6 flops per complex multiply; bytes that the pass must move).
 template <int MODE, class O>
-static void launch_first_last(const BlueGeom& g, const BlueIO& io, int ntrans, cudaStream_t s) {
+static const char* pass_name(const char* pass, std::string& nm) {
   const bool df = std::is_same<O, OpsDF>::value;
+  const char* sfx = MODE == kModeFilter ? "filter" : (MODE == kModeRecon ? "recon" : "eval");
+  nm = std::string("blue_") + pass + "_" + sfx + (df ? "_df" : "");
+  return nm.c_str();
+}
+
+// The 4-step passes with the tiles in g.ctile / g.rtile.  ev (optional):
+// events recorded before the column pass and after each pass.
+template <int MODE, class O>
+static void launch_passes(const BlueGeom& g, const BlueIO& io, int ntrans, cudaStream_t s, cudaEvent_t* ev) {
   const double P = g.P, nr = (double)ntrans / g.L, sumM = (double)g.sum_M;
   const double cb = sizeof(cplx);
-  const char* sfx = MODE == kModeFilter ? "filter" : (MODE == kModeRecon ? "recon" : "eval");
   std::string nm;
-  auto name = [&](const char* pass) {
-    nm = std::string("blue_") + pass + "_" + sfx + (df ? "_df" : "");
-    return nm.c_str();
-  };
-  if (g.P <= kSmallMax) {
-    size_t smem = (size_t)g.P * sizeof(cplx);
-    set_smem(blue_small_kernel<MODE, O>, smem);
-    double fl = ntrans * (MODE == kModeFilter ? fft_flops(P) : 2 * fft_flops(P) + 6 * P) + nr * 6 * sumM;
-    double by = MODE == kModeFilter ? g.L * P * cb + sumM * cb : nr * sumM * cb * 3 + ntrans * P * cb;
-    MR1L_LAUNCH(name("small"), s, fl, by, blue_small_kernel<MODE, O><<<ntrans, threads_for(g.P), smem, s>>>(g, io));
-    return;
-  }
-  int CB = col_tile(g.P1), RB = row_tile(g.P2);
+  int CB = col_tile(g.P1, g.ctile), RB = row_tile(g.P2, g.P1, g.rtile);
+  MR1L_REQUIRE(g.P2 % CB == 0 && g.P1 % RB == 0, "tile does not divide the 4-step split");
   size_t smem_c = (size_t)g.P1 * CB * sizeof(cplx);
   size_t smem_r = (size_t)RB * g.P2 * sizeof(cplx);
   dim3 gc(g.P2 / CB, ntrans), gr(g.P1 / RB, ntrans);
   const double P1 = g.P1, P2 = g.P2;
+  if (ev) MR1L_CUDA(cudaEventRecord(ev[0], s));
   set_smem(blue_col_fwd_kernel<MODE, O>, smem_c);
-  MR1L_LAUNCH(name("col_fwd"), s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM,
+  MR1L_LAUNCH((pass_name<MODE, O>("col_fwd", nm)), s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM,
               nr * sumM * cb * 2 + ntrans * P * cb,
               blue_col_fwd_kernel<MODE, O><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
+  if (ev) MR1L_CUDA(cudaEventRecord(ev[1], s));
   if (MODE == kModeFilter) {
     set_smem(blue_row_kernel<true, O>, smem_r);
-    MR1L_LAUNCH(name("row"), s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
+    MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
                 blue_row_kernel<true, O><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
+    if (ev) {
+      MR1L_CUDA(cudaEventRecord(ev[2], s));
+      MR1L_CUDA(cudaEventRecord(ev[3], s));
+    }
     return;
   }
   set_smem(blue_row_kernel<false, O>, smem_r);
-  MR1L_LAUNCH(name("row"), s, ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
+  MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
               blue_row_kernel<false, O><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
+  if (ev) MR1L_CUDA(cudaEventRecord(ev[2], s));
   set_smem(blue_col_inv_kernel<MODE, O>, smem_c);
-  MR1L_LAUNCH(name("col_inv"), s, ntrans * P2 * fft_flops(P1) + (MODE == kModeEval ? nr * 6 * sumM : 0.0),
+  MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s,
+              ntrans * P2 * fft_flops(P1) + (MODE == kModeEval ? nr * 6 * sumM : 0.0),
               ntrans * P * cb + nr * sumM * cb * (MODE == kModeEval ? 2 : 1),
               blue_col_inv_kernel<MODE, O><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
+  if (ev) MR1L_CUDA(cudaEventRecord(ev[3], s));
+}
+
+// ---------------------------------------------------------------------------
+// Tile tuner.  The first 4-step transform of each (device, P, mode,
+// arithmetic) runs the three passes once with the default tiles, then once
+// per distinct candidate tiling, timed with events on its own stream, and
+// keeps the fastest column tile (column
+// passes together) and row tile; later transforms reuse the choice.  Every
+// tiling computes the same operations in the same order, so the outputs are
+// identical bit for bit and the last trial's output stands.  The trials
+// synchronise the stream once; a stream being captured, or a caller that
+// disables tuning (BlueIO::no_tune, mr1l_tune_enable(0)), gets the default.
+// ---------------------------------------------------------------------------
+struct TileChoice {
+  int ctile, rtile;
+  float col_ms, row_ms;
+};
+static std::mutex g_tile_mu;
+static std::map<std::tuple<int, int, int, int>, TileChoice> g_tiles;  // (device, P, mode, df)
+static int g_tune_on = -1;                                            // -1: read MR1L_TILE_TUNE
+
+static bool tuning_enabled() {
+  if (g_tune_on < 0) {
+    const char* e = std::getenv("MR1L_TILE_TUNE");
+    g_tune_on = (e && e[0] == '0') ? 0 : 1;
+  }
+  return g_tune_on != 0;
+}
+
+struct EventSet {
+  std::vector<cudaEvent_t> ev;
+  explicit EventSet(size_t n) : ev(n, nullptr) {
+    for (auto& e : ev) MR1L_CUDA(cudaEventCreate(&e));
+  }
+  ~EventSet() {
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+template <int MODE, class O>
+static void launch_first_last(const BlueGeom& g, const BlueIO& io, int ntrans, cudaStream_t s) {
+  if (g.P <= kSmallMax) {
+    const double P = g.P, nr = (double)ntrans / g.L, sumM = (double)g.sum_M;
+    const double cb = sizeof(cplx);
+    std::string nm;
+    size_t smem = (size_t)g.P * sizeof(cplx);
+    set_smem(blue_small_kernel<MODE, O>, smem);
+    double fl = ntrans * (MODE == kModeFilter ? fft_flops(P) : 2 * fft_flops(P) + 6 * P) + nr * 6 * sumM;
+    double by = MODE == kModeFilter ? g.L * P * cb + sumM * cb : nr * sumM * cb * 3 + ntrans * P * cb;
+    MR1L_LAUNCH((pass_name<MODE, O>("small", nm)), s, fl, by,
+                blue_small_kernel<MODE, O><<<ntrans, threads_for(g.P), smem, s>>>(g, io));
+    return;
+  }
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, g.P, MODE, (int)std::is_same<O, OpsDF>::value);
+  BlueGeom gg = g;
+  gg.ctile = gg.rtile = kTileElems;
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tiles.find(key);
+    if (it != g_tiles.end()) {
+      gg.ctile = it->second.ctile;
+      gg.rtile = it->second.rtile;
+      launch_passes<MODE, O>(gg, io, ntrans, s, nullptr);
+      return;
+    }
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  MR1L_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (io.no_tune || !tuning_enabled() || cap != cudaStreamCaptureStatusNone) {
+    launch_passes<MODE, O>(gg, io, ntrans, s, nullptr);
+    return;
+  }
+  // distinct candidate tilings (equal CB and RB give the same launch)
+  std::vector<int> cands;
+  std::vector<std::pair<int, int>> seen;
+  for (int t : kTileCands) {
+    auto cr = std::make_pair(col_tile(g.P1, t), row_tile(g.P2, g.P1, t));
+    if (std::find(seen.begin(), seen.end(), cr) == seen.end()) {
+      seen.push_back(cr);
+      cands.push_back(t);
+    }
+  }
+  // one untimed run first: it pays the kernels' first-launch costs and leaves
+  // every timed trial the same cache state
+  launch_passes<MODE, O>(gg, io, ntrans, s, nullptr);
+  EventSet es(4 * cands.size());
+  for (size_t i = 0; i < cands.size(); ++i) {
+    gg.ctile = gg.rtile = cands[i];
+    launch_passes<MODE, O>(gg, io, ntrans, s, &es.ev[4 * i]);
+  }
+  MR1L_CUDA(cudaEventSynchronize(es.ev.back()));
+  TileChoice best{kTileElems, kTileElems, 1e30f, 1e30f};
+  for (size_t i = 0; i < cands.size(); ++i) {
+    float c1 = 0, r = 0, c2 = 0;
+    MR1L_CUDA(cudaEventElapsedTime(&c1, es.ev[4 * i], es.ev[4 * i + 1]));
+    MR1L_CUDA(cudaEventElapsedTime(&r, es.ev[4 * i + 1], es.ev[4 * i + 2]));
+    MR1L_CUDA(cudaEventElapsedTime(&c2, es.ev[4 * i + 2], es.ev[4 * i + 3]));
+    if (c1 + c2 < best.col_ms) {
+      best.col_ms = c1 + c2;
+      best.ctile = cands[i];
+    }
+    if (r < best.row_ms) {
+      best.row_ms = r;
+      best.rtile = cands[i];
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  g_tiles.emplace(key, best);
+}
+
+void tune_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  g_tune_on = on ? 1 : 0;
+}
+
+void tune_reset() {
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  g_tiles.clear();
+}
+
+std::string tune_json() {
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  static const char* modes[3] = {"filter", "recon", "eval"};
+  std::string out = "[";
+  char buf[256];
+  for (const auto& kv : g_tiles) {
+    std::snprintf(buf, sizeof buf,
+                  "%s{\"device\": %d, \"P\": %d, \"mode\": \"%s\", \"df\": %d, \"col_tile\": %d, \"row_tile\": %d, "
+                  "\"col_ms\": %.4f, \"row_ms\": %.4f}",
+                  out.size() > 1 ? ", " : "", std::get<0>(kv.first), std::get<1>(kv.first),
+                  modes[std::get<2>(kv.first)], std::get<3>(kv.first), kv.second.ctile, kv.second.rtile,
+                  kv.second.col_ms, kv.second.row_ms);
+    out += buf;
+  }
+  return out + "]";
 }
 
 void blue_filter(const BlueGeom& g, cudaStream_t s) {
@@ -721,107 +901,164 @@ void blue_filter(const BlueGeom& g, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Lattice noise: y[h][off_l + j] += sigma/sqrt(2) (g1 + i g2) by Box-Muller on
-// the Philox words of sample j (purpose 5; node 0 shared by all lattices).
+// the Philox words of sample j (purpose 5; node 0 shared by all lattices):
+// u1 = Q 2^-53 with Q = (a >> 11) + 1 in [1, 2^53], u2 = B 2^-53 with
+// B = b >> 11, g1 + i g2 = sqrt(-2 ln u1) e^{2 pi i u2}.
 //
-// The logarithm and the sine/cosine are table driven so that the FP64 pipe
-// does little work per sample:
-//   ln u = E ln2 + ln c_k + log1p(r),  u = 2^E m with m in [3/4, 3/2),
-//     c_k = 1 + trunc(128 (m - 1)) / 128 (so c = 1 for m near 1 and the result
-//     keeps its relative accuracy there), r = (m - c_k) / c_k with m - c_k
-//     exact, |r| < 1/96, log1p by its Taylor series to degree 9 (Tang's
-//     table-driven logarithm, ACM TOMS 16(4), 1990);
-//   2 pi u = 2 pi q / 256 + x,  x in [0, 2 pi / 256): sin and cos of x by
-//     their Taylor series (degrees 7 and 8), combined with the tabulated
-//     sin / cos of 2 pi q / 256 by the angle-addition formulas.
-// Both stay within a few units in the last place of FP64.
+// The draws are evaluated in double-float arithmetic (arith.cuh) on the FP32
+// pipes, from the integers Q and B, with table-driven functions:
+//   ln u1 = E ln2 + ln c_k + log1p(r): Q = 2^e m with m in [3/4, 3/2),
+//     E = e - 53, c_k = 1 + k / 4096 with k = trunc(4096 (m - 1)) (so c = 1 for
+//     m near 1 and the result keeps its relative accuracy there),
+//     r = (m - c_k) / c_k where 2^e (m - c_k) is an exact integer, |r| < 2^-11.5,
+//     log1p(r) = r - r^2/2 + r^3/3 - r^4/4 + r^5/5 (Tang's table-driven
+//     logarithm, ACM TOMS 16(4), 1990);
+//   sqrt by one Newton correction of the FP32 square root in double-float;
+//   2 pi u2 = 2 pi q / 256 + x with q = B >> 45 and x in [0, 2 pi / 256) from
+//     the low 45 bits (exact in double-float); sin x and cos x by their Taylor
+//     series to degrees 7 and 8, combined with the tabulated sin / cos of
+//     2 pi q / 256 by the angle-addition formulas.
+// Terms of the series below about 2^-22 relative are summed in plain FP32.
+// The result is within about 2^-46 of |g1 + i g2| (the FP64 draws of the
+// oracle differ from it by no more than that); only the final conversion to
+// FP64 uses the FP64 pipe.
 // ---------------------------------------------------------------------------
-constexpr int kLnTab = 96, kScTab = 256;
+constexpr int kLnCells = 4096;                   // cells per unit of m
+constexpr int kLnTab = 3 * kLnCells / 4;          // k in [-kLnCells/4, kLnCells/2)
+constexpr int kScTab = 256;
 
 struct NoiseTables {
-  double inv_c[kLnTab], ln_c[kLnTab];
-  double sn[kScTab], cs[kScTab];
+  float4 ln[kLnTab];  // (ln c).hi, (ln c).lo, (1/c).hi, (1/c).lo for c = 1 + (i - kLnCells/4) / kLnCells
+  float4 sc[kScTab];  // sin.hi, sin.lo, cos.hi, cos.lo of 2 pi i / kScTab
 };
 
+__device__ __forceinline__ float2 split_df(double x) {
+  float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
 __global__ void noise_tables_kernel(NoiseTables* t) {
-  int i = threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < kLnTab) {
-    double c = 1.0 + (double)(i - 32) / 128.0;  // exact
-    t->inv_c[i] = 1.0 / c;
-    t->ln_c[i] = log(c);
+    double c = 1.0 + (double)(i - kLnCells / 4) / (double)kLnCells;  // exact
+    float2 lc = split_df(log(c)), ic = split_df(1.0 / c);
+    t->ln[i] = make_float4(lc.x, lc.y, ic.x, ic.y);
   }
   if (i < kScTab) {
     double sn, cs;
     sincospi(2.0 * (double)i / kScTab, &sn, &cs);
-    t->sn[i] = sn;
-    t->cs[i] = cs;
+    float2 a = split_df(sn), b = split_df(cs);
+    t->sc[i] = make_float4(a.x, a.y, b.x, b.y);
   }
 }
 
-// ln u for u in (0, 1] (normal doubles)
-__device__ __forceinline__ double ln_unit(double u, const NoiseTables& T) {
-  const double LN2 = 0.69314718055994530942;
-  long long b = __double_as_longlong(u);
-  int E = (int)((b >> 52) & 0x7ff) - 1023;
-  double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);  // [1, 2)
-  if (m >= 1.5) {
-    m *= 0.5;  // exact
-    E += 1;
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }  // |e| <= 126
+
+// ln(Q 2^-53) for Q in [1, 2^53] as a double-float (<= 0)
+__device__ __forceinline__ void ln_q53(uint64_t Q, const NoiseTables* T, float& lh, float& ll) {
+  int e = 63 - __clzll((long long)Q);           // Q in [2^e, 2^(e+1))
+  if (e > 0 && (Q >> (e - 1)) >= 3) ++e;        // m = Q / 2^e in [3/4, 3/2)
+  const long long num = (long long)Q - (1LL << e);  // 2^e (m - 1)
+  int k;
+  long long D;                                   // 2^e (m - c_k), exact
+  if (e >= 12) {
+    const int sh = e - 12;
+    const long long a = num < 0 ? -num : num;
+    const long long kq = a >> sh;                // trunc(4096 |m - 1|)
+    k = (int)(num < 0 ? -kq : kq);
+    D = num - (long long)k * (1LL << sh);
+  } else {
+    k = (int)(num * (1LL << (12 - e)));          // m is a cell point
+    D = 0;
   }
-  const double d = m - 1.0;                     // exact
-  const int k = 32 + (int)trunc(d * 128.0);     // table cell, c_k = 1 + (k - 32) / 128
-  const double c = 1.0 + (double)(k - 32) * 0.0078125;
-  const double r = (m - c) * T.inv_c[k];        // m - c exact
-  // log1p(r) = r - r^2/2 + r^3/3 - ... + r^9/9
-  double p = fma(r, 1.0 / 9.0, -1.0 / 8.0);
-  p = fma(r, p, 1.0 / 7.0);
-  p = fma(r, p, -1.0 / 6.0);
-  p = fma(r, p, 1.0 / 5.0);
-  p = fma(r, p, -1.0 / 4.0);
-  p = fma(r, p, 1.0 / 3.0);
-  p = fma(r, p, -0.5);
-  p = fma(r * r, p, r);
-  return fma((double)E, LN2, T.ln_c[k] + p);
+  // D (|D| < 2^42) as an exact double-float, scaled by 2^-e
+  const long long dq = D / (1LL << 21);          // truncates: dq and the rest share D's sign
+  float dh, dl;
+  two_sum((float)(int)dq * 2097152.0f, (float)(int)(D - dq * (1LL << 21)), dh, dl);
+  const float sc = pow2f(-e);
+  const float4 tk = __ldg(&T->ln[k + kLnCells / 4]);
+  float rh, rl;
+  dw_mul(dh * sc, dl * sc, tk.z, tk.w, rh, rl);  // r = (m - c) / c
+  // log1p(r): r - r^2/2 in double-float, the rest in FP32
+  const float p = __fmul_rn(rh, rh);
+  float pe = __fmaf_rn(rh, rh, -p);
+  pe = __fmaf_rn(2.0f * rh, rl, pe);
+  float tail = __fmaf_rn(rh, 0.2f, -0.25f);
+  tail = __fmaf_rn(rh, tail, 0.33333334f);
+  tail = __fmul_rn(__fmul_rn(rh, p), tail);
+  float ah, al;
+  dw_add(rh, rl, -0.5f * p, -0.5f * pe, ah, al);
+  dw_add(ah, al, tail, 0.0f, ah, al);
+  // + E ln2 + ln c
+  float eh, el;
+  dw_mul((float)(e - 53), 0.0f, 0x1.62e430p-1f, -0x1.05c610p-29f, eh, el);
+  dw_add(eh, el, tk.x, tk.y, eh, el);
+  dw_add(eh, el, ah, al, lh, ll);
 }
 
-// (sin, cos) of 2 pi u for u in [0, 1) on the 2^-53 grid
-__device__ __forceinline__ void sincos_2pi(double u, const NoiseTables& T, double& s, double& c) {
-  const double K = 0.024543692606170259675;  // 2 pi / 256
-  double v = u * kScTab;                     // exact
-  double q = floor(v);
-  int iq = (int)q;
-  double x = (v - q) * K;
-  double x2 = x * x;
-  double ps = fma(x2, -1.0 / 5040.0, 1.0 / 120.0);
-  ps = fma(x2, ps, -1.0 / 6.0);
-  double sx = fma(x * x2, ps, x);
-  double pc = fma(x2, 1.0 / 40320.0, -1.0 / 720.0);
-  pc = fma(x2, pc, 1.0 / 24.0);
-  pc = fma(x2, pc, -0.5);
-  double cx = fma(x2, pc, 1.0);
-  double sq = T.sn[iq], cq = T.cs[iq];
-  s = fma(sq, cx, cq * sx);
-  c = fma(cq, cx, -sq * sx);
+// sqrt of a non-negative double-float
+__device__ __forceinline__ void dw_sqrt(float xh, float xl, float& sh, float& sl) {
+  const float s = __fsqrt_rn(xh);
+  if (!(s > 0.0f)) {
+    sh = 0.0f;
+    sl = 0.0f;
+    return;
+  }
+  const float p = __fmul_rn(s, s), pe = __fmaf_rn(s, s, -p);  // s^2 = p + pe
+  const float d = __fadd_rn(__fsub_rn(__fsub_rn(xh, p), pe), xl);
+  fast_two_sum(s, __fmul_rn(d, __frcp_rn(2.0f * s)), sh, sl);
 }
 
-__global__ void __launch_bounds__(256) lattice_noise_kernel(BlueGeom g, BlueIO io, const NoiseTables* tabs) {
-  __shared__ NoiseTables T;
-  for (int i = threadIdx.x; i < (int)(sizeof(NoiseTables) / sizeof(double)); i += blockDim.x)
-    ((double*)&T)[i] = ((const double*)tabs)[i];
-  __syncthreads();
+// (sin, cos) of 2 pi B 2^-53 for B in [0, 2^53), as double-floats
+__device__ __forceinline__ void sincos_b53(uint64_t B, const NoiseTables* T, float2& sn, float2& cs) {
+  const int q = (int)(B >> 45);
+  const uint64_t F = B & ((1ull << 45) - 1);     // x = 2 pi F 2^-45 / 256
+  float fh, fl;
+  two_sum((float)(uint32_t)(F >> 21) * 0x1p-24f, (float)(uint32_t)(F & 0x1fffff) * 0x1p-45f, fh, fl);
+  float th, tl;
+  dw_mul(fh, fl, 0x1.921fb6p-6f, -0x1.777a5cp-31f, th, tl);  // 2 pi / 256
+  float zh, zl;
+  dw_mul(th, tl, th, tl, zh, zl);                // x^2
+  // sin x = x (1 - x^2/6 + x^4/120 - x^6/5040)
+  float ts = __fmaf_rn(zh, -1.0f / 5040.0f, 1.0f / 120.0f);
+  ts = __fmul_rn(__fmul_rn(zh, zh), ts);
+  float ah, al;
+  dw_mul(zh, zl, 0x1.555556p-3f, -0x1.555556p-28f, ah, al);  // x^2 / 6
+  dw_add(1.0f, 0.0f, -ah, -al, ah, al);
+  dw_add(ah, al, ts, 0.0f, ah, al);
+  float sxh, sxl;
+  dw_mul(th, tl, ah, al, sxh, sxl);
+  // cos x = 1 - x^2/2 + x^4/24 - x^6/720 + x^8/40320
+  float tc = __fmaf_rn(zh, 1.0f / 40320.0f, -1.0f / 720.0f);
+  tc = __fmaf_rn(zh, tc, 1.0f / 24.0f);
+  tc = __fmul_rn(__fmul_rn(zh, zh), tc);
+  float cxh, cxl;
+  dw_add(1.0f, 0.0f, -0.5f * zh, -0.5f * zl, cxh, cxl);
+  dw_add(cxh, cxl, tc, 0.0f, cxh, cxl);
+  const float4 tq = __ldg(&T->sc[q]);            // sin, cos of 2 pi q / 256
+  dw_dot2(tq.x, tq.y, cxh, cxl, tq.z, tq.w, sxh, sxl, 1.0f, sn.x, sn.y);
+  dw_dot2(tq.z, tq.w, cxh, cxl, tq.x, tq.y, sxh, sxl, -1.0f, cs.x, cs.y);
+}
+
+__global__ void __launch_bounds__(256) lattice_noise_kernel(BlueGeom g, BlueIO io, const NoiseTables* T, float sch,
+                                                           float scl) {
   const int l = blockIdx.y, h = blockIdx.z;
   const int M = g.M[l];
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= M) return;
   U64Pair u = philox_u64(io.noise_seed, kNoiseLattice, (uint32_t)io.noise_t, (uint32_t)j, j == 0 ? 0u : (uint32_t)l,
                          (uint32_t)(io.noise_rep + h * io.noise_rep_per_rhs));
-  double u1 = ((double)(u.a >> 11) + 1.0) * 0x1.0p-53;
-  double u2 = (double)(u.b >> 11) * 0x1.0p-53;
-  double R = sqrt(fmax(-2.0 * ln_unit(u1, T), 0.0));  // ln 1 may round to a tiny positive value
-  double sn, cs;
-  sincos_2pi(u2, T, sn, cs);
+  float lh, ll, Rh, Rl;
+  ln_q53((u.a >> 11) + 1, T, lh, ll);
+  dw_sqrt(-2.0f * lh, -2.0f * ll, Rh, Rl);
+  float2 sn, cs;
+  sincos_b53(u.b >> 11, T, sn, cs);
+  dw_mul(Rh, Rl, sch, scl, Rh, Rl);
+  float reh, rel, imh, iml;
+  dw_mul(Rh, Rl, cs.x, cs.y, reh, rel);
+  dw_mul(Rh, Rl, sn.x, sn.y, imh, iml);
+  const cplx e = cmake((double)reh + (double)rel, (double)imh + (double)iml);
   cplx* y = io.out + h * io.out_stride + g.off[l] + j;
-  const double sc = io.noise_scale;
-  const cplx e = cmake(sc * (R * cs), sc * (R * sn));
   *y = io.noise_write ? e : cadd(*y, e);
 }
 
@@ -836,7 +1073,8 @@ static const NoiseTables* noise_tables(cudaStream_t s) {
   if (it != g_noise_tabs.end()) return it->second;
   NoiseTables* t = nullptr;
   MR1L_CUDA(cudaMalloc(&t, sizeof(NoiseTables)));
-  MR1L_LAUNCH("noise_tables_kernel", s, 0, (double)sizeof(NoiseTables), noise_tables_kernel<<<1, 256, 0, s>>>(t));
+  MR1L_LAUNCH("noise_tables_kernel", s, 0, (double)sizeof(NoiseTables),
+              noise_tables_kernel<<<cdiv(kLnTab, 256), 256, 0, s>>>(t));
   MR1L_CUDA(cudaStreamSynchronize(s));
   g_noise_tabs[dev] = t;
   return t;
@@ -847,7 +1085,10 @@ void add_lattice_noise(const BlueGeom& g, const BlueIO& io, int nrhs, cudaStream
   int maxM = (int)std::min<int64_t>(g.sum_M, g.P / 2 + 1);
   dim3 grid(cdiv(maxM, 256), g.L, nrhs);
   const NoiseTables* tabs = noise_tables(s);
-  MR1L_LAUNCH("lattice_noise_kernel", s, 0, 32.0 * nrhs * g.sum_M, lattice_noise_kernel<<<grid, 256, 0, s>>>(g, io, tabs));
+  const float sch = static_cast<float>(io.noise_scale);
+  const float scl = static_cast<float>(io.noise_scale - (double)sch);
+  MR1L_LAUNCH("lattice_noise_kernel", s, 0, 32.0 * nrhs * g.sum_M,
+              lattice_noise_kernel<<<grid, 256, 0, s>>>(g, io, tabs, sch, scl));
 }
 
 void blue_run(const BlueGeom& g, const BlueIO& io, int mode, int nrhs, cudaStream_t s) {

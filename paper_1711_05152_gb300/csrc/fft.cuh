@@ -3,6 +3,8 @@
 // evaluation), in FP64 or in double-float arithmetic on the FP32 pipes.
 #pragma once
 
+#include <string>
+
 #include "common.cuh"
 
 namespace mr1l {
@@ -35,6 +37,9 @@ struct BlueGeom {
   const float4* ws_df;
   const float4* tw_df;
   const float4* twn_df;
+  // complex elements per CTA tile of the column / row passes (set per launch
+  // by the tile tuner)
+  int ctile, rtile;
 };
 
 struct BlueIO {
@@ -52,6 +57,7 @@ struct BlueIO {
   uint64_t noise_seed;
   int noise_t, noise_rep;
   int noise_rep_per_rhs;  // rep index = noise_rep + rhs * noise_rep_per_rhs
+  int no_tune;            // 1: never run tiling trials (default tiles unless already tuned)
 };
 
 constexpr int kSmallMax = 4096;  // P <= 4096: one CTA holds the whole transform
@@ -82,6 +88,12 @@ void blue_run(const BlueGeom& g, const BlueIO& io, int mode, int nrhs, cudaStrea
 // y += complex Gaussian noise of every lattice sample (io.out, io.noise_*),
 // using g.L, g.M, g.off and g.sum_M only.
 void add_lattice_noise(const BlueGeom& g, const BlueIO& io, int nrhs, cudaStream_t s);
+
+// Tile tuner: enable/disable trials, forget the choices, and list them as a
+// JSON array of {device, P, mode, df, col_tile, row_tile, col_ms, row_ms}.
+void tune_enable(int on);
+void tune_reset();
+std::string tune_json();
 
 // Chirp tables w and ws for every lattice (w[n] = exp(-pi i (n^2 mod 2M)/M)).
 void chirp_tables(const BlueGeom& g, int64_t sum_M, cudaStream_t s);

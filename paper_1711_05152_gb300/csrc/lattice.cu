@@ -230,34 +230,34 @@ __device__ __forceinline__ cplx planted_weight(const int32_t* f, cplx c, const d
   return cmul(c, cmake(cs, sn));
 }
 
+// one thread per (planted frequency, lattice, right-hand side)
 __global__ void planted_lattice_kernel(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
-                                       const double* anchors, LatticeDev lat, int Luse, const int64_t* off,
-                                       cplx* bins, int64_t bins_stride) {
-  const int h = blockIdx.y;
+                                       const double* anchors, LatticeDev lat, const int64_t* off, cplx* bins,
+                                       int64_t bins_stride) {
+  const int l = blockIdx.y, h = blockIdx.z;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= s_count) return;
   const int32_t* f = freqs + i * d;
-  cplx wv = planted_weight(f, coeffs[i], anchors + (int64_t)h * d, t, d, -1);
-  cplx* B = bins + h * bins_stride;
-  for (int l = 0; l < Luse; ++l) {
-    const int64_t M = lat.M[l];
-    const int64_t* z = lat.z + (int64_t)l * lat.t;
-    int64_t acc = 0;
-    for (int j = 0; j < t; ++j) acc += (int64_t)f[j] * z[j];
-    acc %= M;
-    if (acc < 0) acc += M;
-    double* dst = (double*)(B + off[l] + acc);
-    atomicAdd(dst, wv.x);
-    atomicAdd(dst + 1, wv.y);
-  }
+  const cplx wv = planted_weight(f, coeffs[i], anchors + (int64_t)h * d, t, d, -1);
+  const int64_t M = lat.M[l];
+  const int64_t* z = lat.z + (int64_t)l * lat.t;
+  int64_t acc = 0;
+  for (int j = 0; j < t; ++j) acc += (int64_t)f[j] * z[j];
+  acc %= M;
+  if (acc < 0) acc += M;
+  double* dst = (double*)(bins + h * bins_stride + off[l] + acc);
+  atomicAdd(dst, wv.x);
+  atomicAdd(dst + 1, wv.y);
 }
 
 void planted_lattice_bins(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
                           const double* anchors_dev, int nrhs, const LatticeDev& lat, int Luse,
                           const BlueGeom& g, cplx* bins, int64_t bins_stride, cudaStream_t s) {
   if (s_count == 0) return;
-  MR1L_LAUNCH("planted_lattice_kernel", s, 0, 0, planted_lattice_kernel<<<dim3(cdiv(s_count, 256), nrhs), 256, 0, s>>>(freqs, coeffs, s_count, d, t, anchors_dev,
-                                                                         lat, Luse, g.off, bins, bins_stride));
+  if (Luse == 0 || nrhs == 0) return;
+  MR1L_LAUNCH("planted_lattice_kernel", s, 0, 0,
+              planted_lattice_kernel<<<dim3(cdiv(s_count, 256), Luse, nrhs), 256, 0, s>>>(
+                  freqs, coeffs, s_count, d, t, anchors_dev, lat, g.off, bins, bins_stride));
 }
 
 __global__ void planted_line_bins_kernel(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,

@@ -111,9 +111,18 @@ __global__ void __launch_bounds__(256) sel_hist_kernel(const uint64_t* keys, int
   const uint64_t hi_mask = pass == 0 ? 0ull : (~0ull << (lo + width));
   const uint64_t prefix = S.prefix & hi_mask;
   const uint64_t* kh = keys + h * n;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t k = kh[c];
-    if (k >= thr && (k & hi_mask) == prefix) atomicAdd(&hist[(k >> lo) & (nb - 1)], 1u);
+  // keys of similar magnitude share the top digits, so the lanes of a warp
+  // that hit the same bin are merged into one shared-memory atomic
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x; c0 < n; c0 += stride) {  // same trip count per warp
+    const int64_t c = c0 + threadIdx.x;
+    int bin = -1;
+    if (c < n) {
+      const uint64_t k = kh[c];
+      if (k >= thr && (k & hi_mask) == prefix) bin = (int)((k >> lo) & (nb - 1));
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, bin);
+    if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nb; i += blockDim.x)

@@ -73,3 +73,11 @@ def test_null_plan_is_rejected(lib):
     buf = ctypes.create_string_buffer(256)
     assert lib.mr1l_last_error(buf, 256) == P.MR1L_E_INVAL
     assert b"plan is null" in buf.value
+
+
+def test_tile_tuner_host_controls(lib):
+    P.tune_reset()
+    assert P.tune_read() == []
+    P.tune_enable(False)
+    P.tune_enable(True)
+    assert lib.mr1l_tune_read(None, 0) == P.MR1L_E_INVAL

@@ -1,0 +1,81 @@
+"""The paper's statistical experiments on the GPU path, at a reduced number
+of repetitions, against the values the paper prints (tests/golden): sample
+counts and errors of Table 5.1, the extreme cells of Table 5.2 and the noisy
+r = 5 row of Table 5.4."""
+
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1711_05152_gb300 as P
+import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.lib()
+
+
+def _rows(name):
+    return [[float(x) for x in ln.split()] for ln in open(os.path.join(GOLDEN, name))
+            if ln.strip() and not ln.startswith("#")]
+
+
+def _stats(sigs, **prm):
+    probs = [dict(d=g.d, N=g.N, s=g.s, s_local=g.s, b=10, seed=7000 + i, freqs=g.freqs, coeffs=g.coeffs,
+                  sigma=g.sigma, theta_mode="abs", **prm) for i, g in enumerate(sigs)]
+    outs = P.sfft_dimincr_batch(probs, concurrency=16)
+    res = []
+    for g, o in zip(sigs, outs):
+        truth = {tuple(f): c for f, c in zip(g.freqs.astype(int).tolist(), g.coeffs)}
+        got = {tuple(f): c for f, c in zip(o.freqs.tolist(), o.coeffs)}
+        num = sum(abs(got.get(k, 0) - truth.get(k, 0)) ** 2 for k in set(truth) | set(got))
+        err = np.sqrt(num / sum(abs(c) ** 2 for c in truth.values()))
+        res.append((o.samples, len(set(truth) & set(got)), set(truth) == set(got), err))
+    return res
+
+
+@pytest.mark.parametrize("d", [5, 10, 20])
+def test_table_5_1_samples_and_errors(d):
+    """N = 32, 1000 box coefficients, absolute threshold 1e-12, r = 1: every
+    run recovers the support with errors near machine precision (the paper:
+    <= 5.3e-16), and the largest sample count of 4 runs lies between 60 % and
+    105 % of the paper's maximum over 10 runs."""
+    pmax = {int(r[0]): r[2] for r in _rows("paper_table_5_1.txt") if int(r[1]) == 1000}[d]
+    sigs = [W.planted_signal(d, 32, 1000, seed=7000 + i, model="box") for i in range(4)]
+    res = _stats(sigs, r=1, theta=1e-12)
+    assert all(ok for _, _, ok, _ in res)
+    assert max(e for *_, e in res) < 2e-15
+    mx = max(sm for sm, *_ in res)
+    assert 0.6 * pmax <= mx <= 1.05 * pmax, (mx, pmax)
+
+
+def test_table_5_2_extreme_cells():
+    """d = 5, 1000 unimodular coefficients: r = 1 with delta = 0.3 never
+    detects all frequencies (paper: success rate 0.000, at least 876
+    correct); r = 3 with delta = 1e-2 always does (paper: 1.000)."""
+    sigs = [W.planted_signal(5, 32, 1000, seed=7000 + i, model="unimodular") for i in range(16)]
+    res = _stats(sigs, r=1, theta=0.3)
+    assert not any(ok for _, _, ok, _ in res)
+    assert min(c for _, c, _, _ in res) >= 800
+    res = _stats(sigs, r=3, theta=1e-2)
+    assert all(ok for _, _, ok, _ in res)
+
+
+def test_table_5_4_noisy_row():
+    """d = 10, 1000 unimodular coefficients, 40 dB, r = 5: all frequencies
+    detected in every run (paper: success rate 1.000) and the relative l2
+    error at the noise level (paper: at most 4.3e-4 over 1000 runs)."""
+    sigs = [W.planted_signal(10, 32, 1000, seed=7000 + i, model="unimodular", snr_db=40.0) for i in range(16)]
+    res = _stats(sigs, r=5, theta=1e-12)
+    assert all(ok for _, _, ok, _ in res)
+    assert max(e for *_, e in res) < 2e-3
