@@ -318,11 +318,13 @@ int mr1l_prof_read(char* buf, size_t len);
  * transform of each (device, P, mode, arithmetic) in the process runs its
  * passes once with the default tiles and once per distinct tiling, timed with
  * CUDA events on the caller's stream (which it synchronises once), and keeps
- * the fastest column and row
- * tiles; the output is the same bit for bit under every tiling.  No trials
+ * the fastest column and row tiles; the output is the same bit for bit under
+ * every tiling.  No trials
  * run while the stream is being captured, under mr1l_reconstruct_noalloc, or
  * when tuning is disabled (mr1l_tune_enable(0), or the environment variable
  * MR1L_TILE_TUNE=0): those transforms use 2048 unless a choice is cached.
+ * MR1L_TILES=<col>,<row> (two of 1024, 2048, 4096) fixes the tiles of every
+ * transform instead (no trials, nothing cached).
  * The paper has no counterpart (it concerns the GPU implementation only).
  * mr1l_tune_reset forgets every choice; mr1l_tune_read writes the choices as
  * a JSON array of {"device", "P", "mode", "df", "col_tile", "row_tile",

@@ -168,7 +168,7 @@ struct LatticeWork {
   DevBuf<uint32_t> pre_res, last_res, seen;
   DevBuf<uint64_t> umask;
   DevBuf<int> cover;
-  DevBuf<cplx> w, ws, Bh;
+  DevBuf<cplx> w, ws, Bh, chirp_seed;
   DevBuf<float4> w_df, ws_df;
   int df = 0;  // Bluestein butterflies in double-float arithmetic
   BlueGeom geom{};
@@ -257,7 +257,8 @@ struct LatticeWork {
       geom.tw_df = twiddle_table_df(P, s);
       geom.twn_df = small_twiddles_df(s);
     }
-    chirp_tables(geom, maxM, s);  // writes the double-float copies as well when df
+    chirp_seed.reserve((size_t)Luse * kChirpSeedLen);
+    chirp_tables(geom, maxM, chirp_seed.get(), s);  // writes the double-float copies as well when df
     blue_filter(geom, s);
   }
 };

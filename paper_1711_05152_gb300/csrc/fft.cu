@@ -359,9 +359,18 @@ __host__ __device__ __forceinline__ int row_tile(int P2, int P1, int tile) {
   return p;
 }
 
+// Register budget of the 4-step kernels: the double-float passes wait on
+// memory more than on arithmetic, so they are held to 64 registers (two
+// 512-thread or four 256-thread CTAs per SM; a few bytes spill) for the
+// occupancy; the FP64 passes keep what the compiler picks (up to 128).
+template <class O>
+struct MinBlocks {
+  static constexpr int value = std::is_same<O, OpsDF>::value ? 2 : 1;
+};
+
 // Pass 1: columns, forward, with the 4-step twiddle.
 template <int MODE, class O>
-__global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io) {
+__global__ void __launch_bounds__(512, MinBlocks<O>::value) blue_col_fwd_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -459,7 +468,7 @@ __global__ void __launch_bounds__(512) blue_col_fwd_kernel(BlueGeom g, BlueIO io
 // Pass 2: rows.  FILTER: forward FFT scaled by 1/P into Bh.  Otherwise forward
 // FFT, times Bh, inverse FFT, times conj(w_P^(n2 k1)).
 template <bool FILTER, class O>
-__global__ void __launch_bounds__(512) blue_row_kernel(BlueGeom g, BlueIO io) {
+__global__ void __launch_bounds__(512, MinBlocks<O>::value) blue_row_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -491,7 +500,7 @@ __global__ void __launch_bounds__(512) blue_row_kernel(BlueGeom g, BlueIO io) {
 
 // Pass 3: columns, inverse; natural-order output n = n1 P2 + n2 for n < M.
 template <int MODE, class O>
-__global__ void __launch_bounds__(512) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
+__global__ void __launch_bounds__(512, MinBlocks<O>::value) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -544,18 +553,37 @@ __global__ void small_twiddle_kernel(cplx* tw) {
   tw[i] = cmake(cs, -sn);
 }
 
+// Chirp w[n] = exp(-pi i q / M), q = n^2 mod 2M (exact), as the product of two
+// tabulated factors exp(-pi i (q >> 12) 4096 / M) * exp(-pi i (q & 4095) / M):
+// per-lattice tables of kChirpLo entries each (2M <= 2^24 leaves at most 4096
+// high parts), filled by sincospi of exactly reduced arguments, so that a
+// sample costs one complex product instead of a sine and a cosine.
+constexpr int kChirpLo = 4096;
+
+__global__ void chirp_seed_kernel(cplx* seed, const int* Ms) {
+  const int l = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kChirpSeedLen) return;
+  const int64_t M = Ms[l];
+  const int64_t e = i < kChirpLo ? i : ((int64_t)(i - kChirpLo) * kChirpLo) % (2 * M);  // phase index mod 2M
+  double sn, cs;
+  sincospi((double)e / (double)M, &sn, &cs);
+  seed[(int64_t)l * kChirpSeedLen + i] = cmake(cs, -sn);
+}
+
 __global__ void chirp_kernel(cplx* w, cplx* ws, float4* w_df, float4* ws_df, const int64_t* off, const int* Ms,
-                             int L) {
-  int l = blockIdx.y;
-  int M = Ms[l];
-  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                             const cplx* seed) {
+  __shared__ double inv_M;
+  const int l = blockIdx.y;
+  const int M = Ms[l];
+  if (threadIdx.x == 0) inv_M = 1.0 / (double)M;
+  __syncthreads();
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (n >= M) return;
-  uint64_t q = ((uint64_t)n * (uint64_t)n) % (uint64_t)(2 * (int64_t)M);  // exact n^2 mod 2M
-  double s, c;
-  sincospi((double)q / (double)M, &s, &c);
-  cplx v = cmake(c, -s);  // exp(-pi i q / M)
-  double inv = 1.0 / (double)M;
-  cplx vs = cmake(c * inv, -s * inv);
+  const uint64_t q = ((uint64_t)n * (uint64_t)n) % (uint64_t)(2 * (int64_t)M);  // exact n^2 mod 2M
+  const cplx* sd = seed + (int64_t)l * kChirpSeedLen;
+  const cplx v = cmul(sd[kChirpLo + (q >> 12)], sd[q & (kChirpLo - 1)]);
+  const cplx vs = cmake(v.x * inv_M, v.y * inv_M);
   w[off[l] + n] = v;
   ws[off[l] + n] = vs;
   if (w_df) {  // double-float copies for the double-float passes
@@ -676,11 +704,14 @@ void blue_split(BlueGeom& g, int P) {
   g.P1 = P / g.P2;
 }
 
-void chirp_tables(const BlueGeom& g, int64_t max_M, cudaStream_t s) {
+void chirp_tables(const BlueGeom& g, int64_t max_M, cplx* seed, cudaStream_t s) {
+  MR1L_LAUNCH("chirp_seed_kernel", s, 0, 16.0 * kChirpSeedLen * g.L,
+              chirp_seed_kernel<<<dim3(cdiv(kChirpSeedLen, 256), g.L), 256, 0, s>>>(seed, g.M));
   dim3 grid(cdiv(max_M, 256), g.L);
   MR1L_LAUNCH("chirp_kernel", s, 0, 32.0 * g.sum_M,
-              chirp_kernel<<<grid, 256, 0, s>>>(const_cast<cplx*>(g.w), const_cast<cplx*>(g.ws), const_cast<float4*>(g.w_df),
-                                    const_cast<float4*>(g.ws_df), g.off, g.M, g.L));
+              chirp_kernel<<<grid, 256, 0, s>>>(const_cast<cplx*>(g.w), const_cast<cplx*>(g.ws),
+                                                const_cast<float4*>(g.w_df), const_cast<float4*>(g.ws_df), g.off,
+                                                g.M, seed));
 }
 
 template <typename K>
@@ -759,6 +790,7 @@ static void launch_passes(const BlueGeom& g, const BlueIO& io, int ntrans, cudaS
 // identical bit for bit and the last trial's output stands.  The trials
 // synchronise the stream once; a stream being captured, or a caller that
 // disables tuning (BlueIO::no_tune, mr1l_tune_enable(0)), gets the default.
+// MR1L_TILES=<col>,<row> in the environment fixes the tiles instead.
 // ---------------------------------------------------------------------------
 struct TileChoice {
   int ctile, rtile;
@@ -767,6 +799,7 @@ struct TileChoice {
 static std::mutex g_tile_mu;
 static std::map<std::tuple<int, int, int, int>, TileChoice> g_tiles;  // (device, P, mode, df)
 static int g_tune_on = -1;                                            // -1: read MR1L_TILE_TUNE
+static int g_forced[2] = {-1, -1};                                    // MR1L_TILES=<col>,<row>
 
 static bool tuning_enabled() {
   if (g_tune_on < 0) {
@@ -774,6 +807,24 @@ static bool tuning_enabled() {
     g_tune_on = (e && e[0] == '0') ? 0 : 1;
   }
   return g_tune_on != 0;
+}
+
+// Tiles fixed by the environment (MR1L_TILES=<col>,<row>, each one of the
+// candidates), for reproducible profiles; {0, 0} when unset.
+static std::pair<int, int> forced_tiles() {
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  if (g_forced[0] < 0) {
+    g_forced[0] = g_forced[1] = 0;
+    const char* e = std::getenv("MR1L_TILES");
+    int c = 0, r = 0;
+    if (e && std::sscanf(e, "%d,%d", &c, &r) == 2) {
+      auto ok = [](int t) { return std::find(std::begin(kTileCands), std::end(kTileCands), t) != std::end(kTileCands); };
+      MR1L_REQUIRE(ok(c) && ok(r), "MR1L_TILES must name two of the tile sizes 1024, 2048, 4096");
+      g_forced[0] = c;
+      g_forced[1] = r;
+    }
+  }
+  return {g_forced[0], g_forced[1]};
 }
 
 struct EventSet {
@@ -806,6 +857,13 @@ static void launch_first_last(const BlueGeom& g, const BlueIO& io, int ntrans, c
   const auto key = std::make_tuple(dev, g.P, MODE, (int)std::is_same<O, OpsDF>::value);
   BlueGeom gg = g;
   gg.ctile = gg.rtile = kTileElems;
+  const auto forced = forced_tiles();
+  if (forced.first) {
+    gg.ctile = forced.first;
+    gg.rtile = forced.second;
+    launch_passes<MODE, O>(gg, io, ntrans, s, nullptr);
+    return;
+  }
   {
     std::lock_guard<std::mutex> lk(g_tile_mu);
     auto it = g_tiles.find(key);

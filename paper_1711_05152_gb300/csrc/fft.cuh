@@ -96,6 +96,8 @@ void tune_reset();
 std::string tune_json();
 
 // Chirp tables w and ws for every lattice (w[n] = exp(-pi i (n^2 mod 2M)/M)).
-void chirp_tables(const BlueGeom& g, int64_t sum_M, cudaStream_t s);
+// seed: device scratch of g.L * kChirpSeedLen complex (per-lattice factor tables).
+constexpr int kChirpSeedLen = 8192;
+void chirp_tables(const BlueGeom& g, int64_t max_M, cplx* seed, cudaStream_t s);
 
 }  // namespace mr1l

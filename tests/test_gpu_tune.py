@@ -2,6 +2,8 @@
 times the candidate tilings and keeps the fastest; every tiling must give the
 same output bit for bit, so results with and without tuning are identical."""
 
+import os
+
 import numpy as np
 import pytest
 
@@ -68,3 +70,29 @@ def test_tuned_tiles_give_identical_bits(fft, M, width):
     ml = lattice.MultiLattice([M], [np.array([z])], [lattice.unique_mask(I, [z], M)], True, 1)
     want, _ = lattice.reconstruct(I, ml, [y[0].cpu().numpy()], "fft")
     assert np.max(np.abs(b[0] - want)) / np.max(np.abs(want)) < 1e-10
+
+
+def test_forced_tiles_from_the_environment(tmp_path):
+    """MR1L_TILES fixes the tiles (read once per process): a child process
+    with forced 4096-element column and 1024-element row tiles gives the same
+    bits as this process."""
+    import subprocess
+    import sys
+    M = 1_300_021
+    I = np.arange(-20000, 20000).reshape(-1, 1)
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal((1, M)) + 1j * rng.standard_normal((1, M))
+    np.save(tmp_path / "y.npy", y)
+    pl = P.plan(I, [M], [[7919]])
+    want = pl.reconstruct(torch.from_numpy(y).cuda()).cpu().numpy()
+    code = (
+        "import numpy as np, torch, paper_1711_05152_gb300 as P\n"
+        f"y = np.load(r'{tmp_path / 'y.npy'}')\n"
+        "I = np.arange(-20000, 20000).reshape(-1, 1)\n"
+        f"pl = P.plan(I, [{M}], [[7919]])\n"
+        "np.save(r'%s', pl.reconstruct(torch.from_numpy(y).cuda()).cpu().numpy())\n"
+        "assert P.tune_read() == []\n" % (tmp_path / "got.npy"))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MR1L_TILES="4096,1024", PYTHONPATH=root)
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, cwd=root, timeout=300)
+    np.testing.assert_array_equal(np.load(tmp_path / "got.npy"), want)
