@@ -115,12 +115,15 @@ def _peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+# the sources of the Bluestein kernels whose DRAM traffic profiles/traffic.json records
+KERNEL_SOURCES = ("fft.cu", "fft.cuh", "arith.cuh", "common.cuh")
+
+
 def _src_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1711_05152_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
+    for fn in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -203,7 +206,8 @@ def oracle_sample(name: str, wl, outs) -> dict:
     """The oracle as it stands on a bounded sample of the same workload, its
     time scaled to the full job by the sample counts (the lattice FFT work per
     sample dominates every increment):
-      plain_d10 / large_d25: increments t <= 4 / t <= 3 of the timed signal;
+      plain_d10 / large_d25: increments t <= 6 / t <= 3 of the timed signal
+      (about 10-20 s of one host core);
       batch256: the three signals with the smallest d s (2N+1), complete."""
     from oracle import sfft as osfft
     full_samples = sum(o.samples for o in outs)
@@ -220,7 +224,7 @@ def oracle_sample(name: str, wl, outs) -> dict:
             sample_samples += res.samples
         what = f"oracle on signals {pick} of batch256 (complete solves)"
     else:
-        t_stop = 4 if name == "plain_d10" else 3
+        t_stop = 6 if name == "plain_d10" else 3
         sig, p = wl.items[0]
         res = osfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=wl.seeds[0],
                          t_stop=t_stop)

@@ -228,6 +228,11 @@ typedef struct sfft_params {
     int t_stop;             /* 0: all d increments; 2 <= t_stop < d: stop after increment t_stop
                                and return the projected set I^(1..t_stop) (rows of t_stop
                                components, coefficients zero) - a bounded prefix of the run */
+    int zero_anchors;       /* 1: the anchor components x'_1..x'_d of every line and lattice
+                               pass are 0 instead of Philox draws - the deterministic variant
+                               the paper remarks on in Section 3 for coefficients whose real
+                               parts (or imaginary parts) all share one sign, meant for r = 1;
+                               the lattices are still drawn (Algorithm 1) */
 } sfft_params;
 
 #define SFFT_MAX_STEPS 256

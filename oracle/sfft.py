@@ -172,8 +172,17 @@ def line_coefficients(y: np.ndarray, N: int) -> np.ndarray:
     return (np.exp(-2j * np.pi * ph) @ y) / K
 
 
+def anchor(seed: int, purpose: int, t: int, d: int, i: int, zero: bool) -> np.ndarray:
+    """The anchor x' of pass i (Algorithm 3 steps 1, 2a and 2c): Philox
+    uniforms, or all zeros in the deterministic variant the paper remarks on
+    in Section 3 (same-sign real or imaginary parts, r = 1)."""
+    if zero:
+        return np.zeros(d)
+    return philox.uniform(seed, purpose, t, np.arange(d, dtype=np.uint64), 0, i)
+
+
 def detect_1d(sig, t: int, seed: int, r: int, s_local: int, theta: float, theta_mode: str,
-              dft: str = "fft"):
+              dft: str = "fft", zero_anchors: bool = False):
     """Steps 1 and 2a: r random lines through the t-th coordinate; length-K_t
     DFT with factor 1/K_t; union of the (up to) s_local largest values above
     the threshold.  Returns (sorted k values, min rank gap, min threshold gap)."""
@@ -183,7 +192,7 @@ def detect_1d(sig, t: int, seed: int, r: int, s_local: int, theta: float, theta_
     gr, gt = math.inf, math.inf
     k = np.arange(-N, N + 1, dtype=np.int64)
     for i in range(r):
-        x = philox.uniform(seed, philox.ANCHOR_LINE, t, np.arange(d, dtype=np.uint64), 0, i)
+        x = anchor(seed, philox.ANCHOR_LINE, t, d, i, zero_anchors)
         y = sample_line(sig, t, x, K, dft)
         if sig.sigma > 0:
             y = y + line_noise(seed, t, i, K, sig.sigma)
@@ -205,17 +214,18 @@ def candidates(prefix: np.ndarray, last: np.ndarray) -> np.ndarray:
 
 
 def sfft(sig, s: int, s_local: int, r: int, b: int, theta: float, theta_mode: str,
-         seed: int, dft: str = "fft", t_stop: int | None = None) -> SfftResult:
+         seed: int, dft: str = "fft", t_stop: int | None = None, zero_anchors: bool = False) -> SfftResult:
     """Algorithm 3.  t_stop (optional) ends the run after that dimension
     increment (a bounded sample of the work; the result is then the
-    projected set I^(1..t_stop))."""
+    projected set I^(1..t_stop)).  zero_anchors: every anchor x' is 0 (the
+    deterministic variant of the remark in Section 3)."""
     d = sig.d
     if d < 2:
         raise ValueError("the dimension-incremental method needs d >= 2")
     K = 2 * sig.N + 1
     steps: list[StepStats] = []
     lines = []
-    I1, gr, gt = detect_1d(sig, 1, seed, r, s_local, theta, theta_mode, dft)
+    I1, gr, gt = detect_1d(sig, 1, seed, r, s_local, theta, theta_mode, dft, zero_anchors)
     lines.append(I1)
     samples = r * K
     prefix = I1.reshape(-1, 1)
@@ -223,7 +233,7 @@ def sfft(sig, s: int, s_local: int, r: int, b: int, theta: float, theta_mode: st
     for t in range(2, d + 1):
         if t_stop is not None and t > t_stop:
             break
-        It, gr, gt = detect_1d(sig, t, seed, r, s_local, theta, theta_mode, dft)
+        It, gr, gt = detect_1d(sig, t, seed, r, s_local, theta, theta_mode, dft, zero_anchors)
         lines.append(It)
         rt, st = (r, s_local) if t < d else (1, s)
         J = candidates(prefix, It)
@@ -239,7 +249,7 @@ def sfft(sig, s: int, s_local: int, r: int, b: int, theta: float, theta_mode: st
         detected = np.zeros(n, dtype=bool)
         p = None
         for i in range(rt):
-            x = philox.uniform(seed, philox.ANCHOR_LAT, t, np.arange(d, dtype=np.uint64), 0, i)
+            x = anchor(seed, philox.ANCHOR_LAT, t, d, i, zero_anchors)
             ys = sample_lattice(sig, t, ml, x, dft)
             if sig.sigma > 0:
                 ys = [y + e for y, e in zip(ys, lattice_noise(seed, t, i, ml, sig.sigma))]

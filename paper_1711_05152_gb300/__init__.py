@@ -71,7 +71,8 @@ class sfft_sampler(C.Structure):
 class sfft_params(C.Structure):
     _fields_ = [("d", C.c_int), ("N", C.c_int), ("s", C.c_int64), ("s_local", C.c_int64),
                 ("r", C.c_int), ("b", C.c_int), ("theta", C.c_double), ("theta_mode", C.c_int),
-                ("seed", C.c_uint64), ("batch_reps", C.c_int), ("fft_arith", C.c_int), ("t_stop", C.c_int)]
+                ("seed", C.c_uint64), ("batch_reps", C.c_int), ("fft_arith", C.c_int), ("t_stop", C.c_int),
+                ("zero_anchors", C.c_int)]
 
 
 class sfft_step_stats(C.Structure):
@@ -298,13 +299,16 @@ class SfftOutput:
 def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str = "rel", seed: int = 0,
                  s_local: int | None = None, b: int = 10, freqs=None, coeffs=None, sigma: float = 0.0,
                  noise_seed: int | None = None, sampler=None, batch_reps: bool = False,
-                 t_stop: int | None = None, fft: str = "f64", stream=None) -> SfftOutput:
+                 t_stop: int | None = None, fft: str = "f64", zero_anchors: bool = False,
+                 stream=None) -> SfftOutput:
     """Algorithm 3.  Either a planted polynomial (freqs [s, d], coeffs [s],
     sigma) evaluated by the library, or ``sampler(req, y_ptr, stream_ptr)``,
-    a Python callable that fills the device buffer y_ptr for a request."""
+    a Python callable that fills the device buffer y_ptr for a request.
+    zero_anchors: the deterministic variant (anchors 0, see sfft_params)."""
     p = sfft_params(d=d, N=N, s=s, s_local=s if s_local is None else s_local, r=r, b=b, theta=theta,
                     theta_mode=SFFT_THETA_REL if theta_mode == "rel" else SFFT_THETA_ABS, seed=seed,
-                    batch_reps=1 if batch_reps else 0, fft_arith=1 if fft == "df" else 0, t_stop=t_stop or 0)
+                    batch_reps=1 if batch_reps else 0, fft_arith=1 if fft == "df" else 0, t_stop=t_stop or 0,
+                    zero_anchors=1 if zero_anchors else 0)
     keep = []
     nseed = seed if noise_seed is None else noise_seed
     if sampler is None and getattr(freqs, "is_cuda", False):
@@ -359,7 +363,7 @@ def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[Sfft
     """Algorithm 3 on many independent planted problems at once.  Each problem
     is a dict with d, N, s, r, theta, theta_mode, seed, freqs, coeffs (host
     arrays, or contiguous int32 / complex128 CUDA tensors) and optionally
-    sigma, s_local, b, noise_seed, batch_reps."""
+    sigma, s_local, b, noise_seed, batch_reps, fft, zero_anchors."""
     n = len(problems)
     params = (sfft_params * max(n, 1))()
     samps = (sfft_sampler * max(n, 1))()
@@ -370,7 +374,8 @@ def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[Sfft
                                 b=q.get("b", 10), theta=q["theta"],
                                 theta_mode=SFFT_THETA_REL if q.get("theta_mode", "rel") == "rel" else SFFT_THETA_ABS,
                                 seed=q["seed"], batch_reps=1 if q.get("batch_reps", True) else 0,
-                                fft_arith=1 if q.get("fft", "f64") == "df" else 0)
+                                fft_arith=1 if q.get("fft", "f64") == "df" else 0,
+                                zero_anchors=1 if q.get("zero_anchors", False) else 0)
         if getattr(q["freqs"], "is_cuda", False):
             f, c = q["freqs"], q["coeffs"]
             keep += [f, c]

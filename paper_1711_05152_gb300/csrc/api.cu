@@ -547,7 +547,8 @@ struct SfftRun {
   }
 
   std::vector<double> anchor_rows(uint32_t purpose, int t, int rep0, int count) {
-    std::vector<double> a((size_t)count * P.d);
+    std::vector<double> a((size_t)count * P.d, 0.0);
+    if (P.zero_anchors) return a;
     for (int i = 0; i < count; ++i)
       for (int j = 0; j < P.d; ++j)
         a[(size_t)i * P.d + j] =
@@ -818,6 +819,7 @@ static void validate_sfft(const sfft_params* params, const sfft_sampler* sampler
   MR1L_REQUIRE(P.theta >= 0.0 && std::isfinite(P.theta), "theta must be finite and >= 0");
   MR1L_REQUIRE(P.theta_mode == SFFT_THETA_ABS || P.theta_mode == SFFT_THETA_REL, "bad theta_mode");
   MR1L_REQUIRE(P.t_stop == 0 || (P.t_stop >= 2 && P.t_stop <= P.d), "t_stop must be 0 or in [2, d]");
+  MR1L_REQUIRE(P.zero_anchors == 0 || P.zero_anchors == 1, "zero_anchors must be 0 or 1");
   MR1L_REQUIRE(P.fft_arith == 0 || P.fft_arith == 1, "fft_arith must be 0 (FP64) or 1 (double-float)");
   if (!sampler->fn) {
     MR1L_REQUIRE(sampler->s >= 0, "planted s must be >= 0");

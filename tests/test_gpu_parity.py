@@ -186,6 +186,21 @@ def test_sfft_plain_d10_parity():
     _assert_sfft_equal(out, ref)
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_sfft_zero_anchors_parity(seed):
+    """The deterministic variant (anchors 0, r = 1) on coefficients with
+    positive real parts, noiseless and at 30 dB, against the oracle."""
+    for snr in (None, 30.0):
+        sig = W.planted_signal(5, 8, 80, seed=seed, model="posre", snr_db=snr)
+        out = P.sfft_dimincr(5, 8, 80, 1, 1e-12, "abs", seed=seed, freqs=sig.freqs, coeffs=sig.coeffs,
+                             sigma=sig.sigma, zero_anchors=True)
+        ref = sfft.sfft(sig, 80, 80, 1, 10, 1e-12, "abs", seed=seed, zero_anchors=True)
+        assert min(st.min_gap_rank for st in ref.steps) > 1e-9, "degenerate seed (near tie)"
+        _assert_sfft_equal(out, ref)
+        if snr is None:
+            np.testing.assert_array_equal(out.freqs, sig.freqs.astype(np.int64))
+
+
 def test_sfft_batched_reps_identical():
     sig, out, ref = _sfft_pair("tiny_d3", 5, batch=True)
     _assert_sfft_equal(out, ref)

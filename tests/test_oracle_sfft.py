@@ -180,3 +180,48 @@ def test_mutation_line_sign(monkeypatch):
     monkeypatch.setattr(sfft, "line_coefficients",
                         lambda y, N: np.fft.ifft(y)[np.mod(np.arange(-N, N + 1), 2 * N + 1)])
     assert not _line_identity_ok()
+
+
+# ----------------------------------------------------------------------------
+# The deterministic variant (anchors fixed to 0; remark in Section 3)
+# ----------------------------------------------------------------------------
+
+def test_zero_anchor_projection_is_the_plain_prefix_sum():
+    """With x' = 0 the projected coefficient of a lattice pass is
+    sum_{h: h_(1..t) = k} c_h (the aliasing identity of Section 4.1 without
+    phases)."""
+    sig = W.planted_signal(4, 6, 60, seed=21, model="posre")
+    t = 2
+    J = sfft.candidates(np.unique(sig.freqs[:, :1].astype(np.int64), axis=0),
+                        np.arange(-sig.N, sig.N + 1, dtype=np.int64))
+    ml = lattice.search(J, 5, t, 10)
+    ys = sfft.sample_lattice(sig, t, ml, np.zeros(4), "direct")
+    p, _ = lattice.reconstruct(J, ml, ys, "direct")
+    want = {}
+    for h, c in zip(sig.freqs.astype(np.int64), sig.coeffs):
+        want[tuple(h[:t])] = want.get(tuple(h[:t]), 0) + c
+    got = {tuple(k): v for k, v in zip(J.tolist(), p)}
+    for k, v in got.items():
+        assert abs(v - want.get(k, 0)) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_zero_anchors_recover_same_sign_real_parts_with_r1(seed):
+    """Coefficients with positive real parts: no prefix sum can vanish, so
+    one pass per increment with x' = 0 finds the whole support."""
+    sig = W.planted_signal(5, 8, 80, seed=seed, model="posre")
+    res = sfft.sfft(sig, 80, 80, 1, 10, 1e-12, "abs", seed=seed, zero_anchors=True)
+    np.testing.assert_array_equal(res.freqs, sig.freqs.astype(np.int64))
+    assert np.max(np.abs(res.coeffs - sig.coeffs) / np.abs(sig.coeffs)) < 1e-13
+
+
+def test_zero_anchors_miss_cancelling_coefficients():
+    """Two frequencies with the same first component and coefficients 1 and
+    -1 cancel in the first line when x' = 0, so the deterministic variant
+    misses both (random anchors find them): the flag really fixes x'."""
+    sig = W.PlantedSignal(d=3, N=4, freqs=np.array([[1, 0, 2], [1, 3, -1]], dtype=np.int32),
+                          coeffs=np.array([1.0, -1.0], dtype=np.complex128))
+    det = sfft.sfft(sig, 2, 2, 1, 10, 1e-9, "abs", seed=3, zero_anchors=True)
+    rnd = sfft.sfft(sig, 2, 2, 1, 10, 1e-9, "abs", seed=3)
+    assert det.freqs.shape[0] == 0
+    np.testing.assert_array_equal(rnd.freqs, sig.freqs.astype(np.int64))

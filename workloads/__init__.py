@@ -75,6 +75,8 @@ def _coefficients(rng: np.random.Generator, s: int, model: str) -> np.ndarray:
     "logu":      amplitude log-uniform on [1e-2, 10], phase ~ U[0, 1)
     "unimodular": a = 1, phase ~ U[0, 1)                  (Sections 5.1.3, 5.2)
     "box":       Re, Im ~ U[-1, 1), redrawn while |c| < 1e-6 (Section 5.1)
+    "posre":     Re ~ U[1e-3, 1), Im ~ U[-1, 1): every real part positive
+                 (the coefficients of the deterministic variant, Section 3)
     """
     if model == "box":
         c = rng.uniform(-1, 1, s) + 1j * rng.uniform(-1, 1, s)
@@ -83,6 +85,8 @@ def _coefficients(rng: np.random.Generator, s: int, model: str) -> np.ndarray:
             c[bad] = rng.uniform(-1, 1, bad.sum()) + 1j * rng.uniform(-1, 1, bad.sum())
             bad = np.abs(c) < 1e-6
         return c.astype(np.complex128)
+    if model == "posre":
+        return (rng.uniform(1e-3, 1, s) + 1j * rng.uniform(-1, 1, s)).astype(np.complex128)
     if model == "u1_10":
         a = rng.uniform(1.0, 10.0, s)
     elif model == "logu":
