@@ -204,7 +204,7 @@ __device__ __forceinline__ void stockham_stage(typename O::V* s, int n, int Ns, 
   for (int c = 0; c < CNT; ++c) {
     if (act[c]) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[base[c] + r * Ns * is] = v[c][r];
+      for (int r = 0; r < R; ++r) s[base[c] + r * Ns * is] = O::norm(v[c][r]);
     }
   }
   __syncthreads();
