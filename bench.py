@@ -496,12 +496,42 @@ def _run_stats(problems, sigs, fft):
             "success_rate": float(np.mean(success)), "max_rel_l2": float(max(err))}
 
 
+def _bspline_l2_error(desc, out) -> float:
+    """Relative L2(T^d) error of a Section 5.3 run (the formula of that
+    section): sqrt(||f||^2 - sum_I |f^_k|^2 + sum_I |p~_k - f^_k|^2) / ||f||
+    with the exact coefficients f^_k = sum_g [k = 0 off S_g] prod_{t in S_g}
+    C_m sinc(pi k_t / m)^m (-1)^k_t, C_m = (m B_2m(m))^-1/2 and
+    ||f||^2 = G + sum_{g != h} C_g^|S_g| C_h^|S_h| (disjoint groups)."""
+    def c_m(m):
+        b2m = sum((-1) ** j * math.comb(2 * m, j) * (m - j) ** (2 * m - 1) for j in range(m + 1))
+        return 1.0 / math.sqrt(m * b2m / math.factorial(2 * m - 1))
+
+    K = np.asarray(out.freqs, dtype=np.int64)
+    fk = np.zeros(K.shape[0])
+    means = []
+    for dims, m in zip(desc.groups, desc.orders):
+        C = c_m(m)
+        means.append(C ** len(dims))
+        off = [t for t in range(desc.d) if t not in dims]
+        val = np.all(K[:, off] == 0, axis=1).astype(np.float64)
+        for t in dims:
+            x = np.pi * K[:, t] / m
+            sinc = np.where(K[:, t] == 0, 1.0, np.sin(x) / np.where(K[:, t] == 0, 1.0, x))
+            val = val * C * sinc ** m * np.where(K[:, t] % 2 == 0, 1.0, -1.0)
+        fk += val
+    n2 = len(means) + sum(a * b for i, a in enumerate(means) for j, b in enumerate(means) if i != j)
+    e2 = n2 - float(np.sum(fk ** 2)) + float(np.sum(np.abs(out.coeffs - fk) ** 2))
+    return math.sqrt(max(e2, 0.0) / n2)
+
+
 def run_paper_table(args):
     """One JSON line per row of the paper's Table 5.1 (samples and errors,
-    Section 5.1), 5.2 (success rates over r and the absolute threshold) or
-    5.4 (noise, Section 5.2), measured on the GPU path with the paper's
-    protocol and seeded synthetic signals, beside the paper's printed values
+    Section 5.1), 5.2 (success rates over r and the absolute threshold), 5.4
+    (noise, Section 5.2) or 5.7 (the B-spline function of Section 5.3,
+    s-sparse), measured on the GPU path with the paper's protocol and seeded
+    synthetic signals, beside the paper's printed values
     (tests/golden/paper_table_*.txt)."""
+    import paper_1711_05152_gb300 as P
     reps, base = args.reps, 1000 * args.seed
     if args.paper_table == "5.1":
         sizes = {int(x) for x in args.sizes.split(",")}
@@ -527,6 +557,23 @@ def run_paper_table(args):
             st = _run_stats(probs, sigs, args.fft)
             print(json.dumps({"paper_table": "5.2", "r": int(r), "delta": delta, "reps": reps, "fft": args.fft,
                               **st, "paper": {"min_correct": int(pmin), "success_rate": prate, "reps": 1000},
+                              "seconds": round(time.time() - t0, 2)}), flush=True)
+    elif args.paper_table == "5.7":
+        # Section 5.3, s-sparse strategy; s_local = 2 s for the intermediate increments
+        for N, s_, pmax, perr in _paper_rows("paper_table_5_7.txt"):
+            N, s_ = int(N), int(s_)
+            t0 = time.time()
+            desc = W.paper_bspline(N)
+            samples, errs = [], []
+            for i in range(reps):
+                o = P.sfft_dimincr(10, N, s_, 5, 1e-12, "abs", seed=base + i, s_local=2 * s_, function=desc,
+                                   batch_reps=True, fft=args.fft)
+                samples.append(o.samples)
+                errs.append(_bspline_l2_error(desc, o))
+            print(json.dumps({"paper_table": "5.7", "N": N, "s": s_, "s_local": 2 * s_, "reps": reps,
+                              "fft": args.fft, "max_samples": int(max(samples)), "max_rel_l2": max(errs),
+                              "paper": {"max_samples": int(pmax), "max_rel_l2": perr},
+                              "samples_over_paper": max(samples) / pmax,
                               "seconds": round(time.time() - t0, 2)}), flush=True)
     else:
         for snr, r, pmax, pmin, prate, perr in _paper_rows("paper_table_5_4.txt"):
@@ -578,7 +625,7 @@ def main():
     ap.add_argument("--fft", default="f64", choices=["f64", "df"], help="arithmetic of --kernel-case and --paper-table")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the lattice transform at the workload size (for ncu captures)")
-    ap.add_argument("--paper-table", choices=["5.1", "5.2", "5.4"],
+    ap.add_argument("--paper-table", choices=["5.1", "5.2", "5.4", "5.7"],
                     help="rerun one of the paper's statistical experiments on the GPU path")
     ap.add_argument("--reps", type=int, default=10, help="repetitions per row of --paper-table")
     ap.add_argument("--sizes", default="1000,10000", help="sparsities of the --paper-table 5.1 rows")

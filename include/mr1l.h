@@ -196,12 +196,24 @@ typedef struct sfft_request {
 
 typedef int (*sfft_sample_fn)(void* user, const sfft_request* req, void* y, void* stream);
 
-/* Sampler: either a user callback, or (fn == NULL) the built-in planted
- * sparse polynomial p(x) = sum_h c_h e^{2 pi i h.x} plus complex Gaussian
- * noise eta = sigma/sqrt(2) (g1 + i g2) (Section 5.2), drawn with Philox
- * purposes 4 and 5 keyed by noise_seed.  The planted sampler evaluates
- * lattices by the Section 4.1 aliasing identity (bin h_(1..t).z_l mod M_l,
- * weight c_h e^{2 pi i h_(>t).x'}) and an inverse Bluestein DFT. */
+#define SFFT_SAMPLER_PLANTED 0
+#define SFFT_SAMPLER_BSPLINE 1
+
+/* Sampler: either a user callback, or (fn == NULL) a built-in one:
+ *
+ * SFFT_SAMPLER_PLANTED (kind 0): the planted sparse polynomial
+ * p(x) = sum_h c_h e^{2 pi i h.x} plus complex Gaussian noise
+ * eta = sigma/sqrt(2) (g1 + i g2) (Section 5.2), drawn with Philox purposes 4
+ * and 5 keyed by noise_seed.  It evaluates lattices by the Section 4.1
+ * aliasing identity (bin h_(1..t).z_l mod M_l, weight c_h e^{2 pi i h_(>t).x'})
+ * and an inverse Bluestein DFT.
+ *
+ * SFFT_SAMPLER_BSPLINE (kind 1): the tensor-product B-spline function of
+ * Section 5.3, f(x) = sum_g prod_{t: group_of[t] = g} N_{orders[g]}(x_t),
+ * N_m(x) = C_m sum_k sinc(pi k/m)^m (-1)^k e^{2 pi i k x} with ||N_m|| = 1,
+ * evaluated at every node in the spatial domain (N_m(x) = C_m m B_m(m x) with
+ * the cardinal B-spline B_m); noiseless (sigma must be 0), freqs/coeffs unused,
+ * orders in [2, 8], at most 8 groups, d <= 64. */
 typedef struct sfft_sampler {
     sfft_sample_fn fn;
     void* user;
@@ -211,6 +223,10 @@ typedef struct sfft_sampler {
     double sigma;
     uint64_t noise_seed;
     int device_arrays;      /* planted: 1 if freqs and coeffs are device pointers */
+    int kind;               /* fn == NULL: SFFT_SAMPLER_PLANTED (0) or SFFT_SAMPLER_BSPLINE */
+    int n_groups;           /* bspline: number of tensor-product terms */
+    const int* group_of;    /* bspline: host int [d]: term of each dimension, or -1 (absent) */
+    const int* orders;      /* bspline: host int [n_groups]: B-spline order of each term */
 } sfft_sampler;
 
 typedef struct sfft_params {

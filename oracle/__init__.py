@@ -18,9 +18,11 @@ lattices"):
   evaluation (Section 4.1 aliasing identity) and its adjoint.
 * ``sfft``    - Algorithm 3 (dimension-incremental sparse FFT), its 1-D
   detection steps and thresholded top-s selection.
+* ``bspline`` - the tensor-product B-spline test function of Section 5.3
+  (spatial-domain evaluation, exact Fourier coefficients, L2 error).
 
 Every function says which passage it follows.  Pins that tie the oracle to
 the paper and to mathematics live in ``tests/test_oracle_*.py``.
 """
 
-from . import philox, lattice, sfft  # noqa: F401
+from . import philox, lattice, sfft, bspline  # noqa: F401

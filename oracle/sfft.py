@@ -44,7 +44,13 @@ def _phase_weights(freqs: np.ndarray, coeffs: np.ndarray, x: np.ndarray, comps) 
 
 
 def sample_line(sig, t: int, x: np.ndarray, K: int, dft: str = "fft") -> np.ndarray:
-    """p(x_1', .., x_{t-1}', l/K, x_{t+1}', .., x_d') for l = 0..K-1 (t is 1-based)."""
+    """p(x_1', .., x_{t-1}', l/K, x_{t+1}', .., x_d') for l = 0..K-1 (t is 1-based).
+    A signal given in the spatial domain (sig.value, e.g. the Section 5.3
+    function) is evaluated at the nodes directly."""
+    if hasattr(sig, "value"):
+        X = np.tile(np.asarray(x, dtype=np.float64), (K, 1))
+        X[:, t - 1] = np.arange(K, dtype=np.float64) / K
+        return sig.value(X)
     others = [j for j in range(sig.d) if j != t - 1]
     w = _phase_weights(sig.freqs, sig.coeffs, x, others)
     ht = sig.freqs[:, t - 1].astype(np.int64)
@@ -61,7 +67,16 @@ def sample_lattice(sig, t: int, ml: lattice.MultiLattice, x: np.ndarray,
     """p(j z_l / M_l mod 1, x_{t+1}', .., x_d') for every lattice l and node j.
     "direct" evaluates p(x) = sum_h c_h e^{2 pi i h.x} at each node; "fft" uses
     the aliasing identity of Section 4.1 (bin h_{1..t}.z_l mod M_l, weight
-    c_h e^{2 pi i h_{>t}.x'}) and a length-M_l inverse library FFT."""
+    c_h e^{2 pi i h_{>t}.x'}) and a length-M_l inverse library FFT.  A
+    spatial-domain signal (sig.value) is evaluated at the nodes directly."""
+    if hasattr(sig, "value"):
+        out = []
+        for M, z in zip(ml.M, ml.z):
+            X = np.tile(np.asarray(x, dtype=np.float64), (M, 1))
+            j = np.arange(M, dtype=np.int64)
+            X[:, :t] = np.mod(np.outer(j, np.asarray(z, dtype=np.int64)), M).astype(np.float64) / M
+            out.append(sig.value(X))
+        return out
     w = _phase_weights(sig.freqs, sig.coeffs, x, range(t, sig.d))
     head = sig.freqs[:, :t].astype(np.int64)
     out = []

@@ -65,7 +65,23 @@ SAMPLE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(sfft_request), C.c_void_p
 class sfft_sampler(C.Structure):
     _fields_ = [("fn", SAMPLE_FN), ("user", C.c_void_p), ("freqs", C.POINTER(C.c_int32)),
                 ("coeffs", C.POINTER(C.c_double)), ("s", C.c_int64), ("sigma", C.c_double),
-                ("noise_seed", C.c_uint64), ("device_arrays", C.c_int)]
+                ("noise_seed", C.c_uint64), ("device_arrays", C.c_int), ("kind", C.c_int),
+                ("n_groups", C.c_int), ("group_of", C.POINTER(C.c_int)), ("orders", C.POINTER(C.c_int))]
+
+
+SFFT_SAMPLER_PLANTED, SFFT_SAMPLER_BSPLINE = 0, 1
+
+
+def _bspline_sampler(d: int, function, keep: list) -> sfft_sampler:
+    """The built-in Section 5.3 sampler for a description with .groups (lists
+    of 0-based dimensions) and .orders (B-spline order per group)."""
+    group_of = np.full(d, -1, dtype=np.int32)
+    for g, dims in enumerate(function.groups):
+        group_of[list(dims)] = g
+    orders = np.ascontiguousarray(np.asarray(function.orders, dtype=np.int32))
+    keep += [group_of, orders]
+    return sfft_sampler(SAMPLE_FN(), None, None, None, 0, 0.0, 0, 0, SFFT_SAMPLER_BSPLINE, len(function.orders),
+                        group_of.ctypes.data_as(C.POINTER(C.c_int)), orders.ctypes.data_as(C.POINTER(C.c_int)))
 
 
 class sfft_params(C.Structure):
@@ -300,10 +316,12 @@ def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str =
                  s_local: int | None = None, b: int = 10, freqs=None, coeffs=None, sigma: float = 0.0,
                  noise_seed: int | None = None, sampler=None, batch_reps: bool = False,
                  t_stop: int | None = None, fft: str = "f64", zero_anchors: bool = False,
-                 stream=None) -> SfftOutput:
+                 function=None, stream=None) -> SfftOutput:
     """Algorithm 3.  Either a planted polynomial (freqs [s, d], coeffs [s],
-    sigma) evaluated by the library, or ``sampler(req, y_ptr, stream_ptr)``,
-    a Python callable that fills the device buffer y_ptr for a request.
+    sigma) evaluated by the library, the Section 5.3 B-spline function
+    (``function`` with .groups and .orders, evaluated by the library), or
+    ``sampler(req, y_ptr, stream_ptr)``, a Python callable that fills the
+    device buffer y_ptr for a request.
     zero_anchors: the deterministic variant (anchors 0, see sfft_params)."""
     p = sfft_params(d=d, N=N, s=s, s_local=s if s_local is None else s_local, r=r, b=b, theta=theta,
                     theta_mode=SFFT_THETA_REL if theta_mode == "rel" else SFFT_THETA_ABS, seed=seed,
@@ -311,7 +329,9 @@ def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str =
                     zero_anchors=1 if zero_anchors else 0)
     keep = []
     nseed = seed if noise_seed is None else noise_seed
-    if sampler is None and getattr(freqs, "is_cuda", False):
+    if function is not None:
+        samp = _bspline_sampler(d, function, keep)
+    elif sampler is None and getattr(freqs, "is_cuda", False):
         # planted signal already resident on the device (int32 [s, d], complex128 [s])
         import torch
         if freqs.dtype != torch.int32 or coeffs.dtype != torch.complex128 or not (

@@ -490,6 +490,52 @@ extern "C" int mr1l_evaluate(mr1l_plan_t* plan, const void* c, int nrhs, void* y
 // ---------------------------------------------------------------------------
 namespace mr1l {
 
+// ---------------------------------------------------------------------------
+// Section 5.3 test function: polynomial pieces of N_m(x) = C_m m B_m(m x)
+// ---------------------------------------------------------------------------
+static int64_t binom_i64(int n, int k) {
+  int64_t r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+static int64_t ipow_i64(int64_t b, int e) {
+  int64_t r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+static double factorial_d(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
+// On [q, q+1), B_m(q + f) = 1/(m-1)! sum_{j<=q} (-1)^j binom(m,j) (q - j + f)^{m-1}
+// (truncated-power form), i.e. sum_k a_{q,k} f^k / (m-1)! with the integers
+// a_{q,k} = binom(m-1,k) sum_{j<=q} (-1)^j binom(m,j) (q-j)^{m-1-k}.
+// C_m^-2 = m B_2m(m) (the autocorrelation of B_m is B_2m), B_2m(m) from the
+// same form in integers.
+static void bspline_tables(const sfft_sampler& S, int d, BsplineDev& B) {
+  std::memset(&B, 0, sizeof(B));
+  B.d = d;
+  B.n_groups = S.n_groups;
+  for (int i = 0; i < d; ++i) B.group_of[i] = S.group_of[i];
+  for (int g = 0; g < S.n_groups; ++g) {
+    const int m = S.orders[g];
+    B.order[g] = m;
+    int64_t s2 = 0;
+    for (int j = 0; j <= m; ++j) s2 += ((j & 1) ? -1 : 1) * binom_i64(2 * m, j) * ipow_i64(m - j, 2 * m - 1);
+    const long double b2m = (long double)s2 / (long double)factorial_d(2 * m - 1);
+    const long double Cm = 1.0L / std::sqrt((long double)m * b2m);
+    const long double scale = Cm * (long double)m / (long double)factorial_d(m - 1);
+    for (int q = 0; q < m; ++q)
+      for (int k = 0; k < m; ++k) {
+        int64_t a = 0;
+        for (int j = 0; j <= q; ++j) a += ((j & 1) ? -1 : 1) * binom_i64(m, j) * ipow_i64(q - j, m - 1 - k);
+        B.coef[g][q][k] = (double)((long double)(a * binom_i64(m - 1, k)) * scale);
+      }
+  }
+}
+
 struct SfftRun {
   sfft_params P;
   sfft_sampler S;
@@ -503,6 +549,10 @@ struct SfftRun {
   DevBuf<cplx> coeffs_buf;
   const int32_t* freqs_ptr = nullptr;
   const cplx* coeffs_ptr = nullptr;
+  // Section 5.3 function sampler
+  bool bspline = false;
+  BsplineDev bs_host;
+  DevBuf<BsplineDev> bs_dev;
   // candidate prefix (device + host mirror) and last list
   DevBuf<int32_t> pre, pre_next, last;
   std::vector<int32_t> pre_h;
@@ -578,6 +628,8 @@ struct SfftRun {
         int rc = S.fn(S.user, &q, line_y.get() + (size_t)i * K, s);
         if (rc != 0) throw Error(MR1L_E_SAMPLER, "sampler callback failed (line request)");
       }
+    } else if (bspline) {
+      bspline_lines(bs_dev.get(), t, K, anchors.get(), r, line_y.get(), s);
     } else {
       planted_lines(freqs_ptr, coeffs_ptr, S.s, P.d, t, K, anchors.get(), r, S.sigma / std::sqrt(2.0),
                     S.noise_seed, 0, line_bins.get(), line_y.get(), s);
@@ -621,6 +673,10 @@ struct SfftRun {
         int rc = S.fn(S.user, &q, y.get() + (size_t)i * sumM, s);
         if (rc != 0) throw Error(MR1L_E_SAMPLER, "sampler callback failed (lattice request)");
       }
+    } else if (bspline) {
+      int maxM = 0;
+      for (int l = 0; l < lw.Luse; ++l) maxM = std::max(maxM, lw.Mh[l]);
+      bspline_lattice(bs_dev.get(), t, anchors.get(), nrep, lw.dev(), lw.Luse, lw.geom, maxM, y.get(), sumM, s);
     } else {
       const bool noisy = S.sigma > 0;
       if (noisy) {
@@ -682,7 +738,12 @@ struct SfftRun {
     lw.df = P.fft_arith ? 1 : 0;
     theta2 = P.theta * P.theta;
     rel = P.theta_mode == SFFT_THETA_REL;
-    if (!S.fn && !S.device_arrays) {
+    bspline = !S.fn && S.kind == SFFT_SAMPLER_BSPLINE;
+    if (bspline) {
+      bspline_tables(S, d, bs_host);
+      bs_dev.reserve(1);
+      MR1L_CUDA(cudaMemcpyAsync(bs_dev.get(), &bs_host, sizeof(BsplineDev), cudaMemcpyHostToDevice, s));
+    } else if (!S.fn && !S.device_arrays) {
       freqs_buf.reserve(std::max<int64_t>(S.s * d, 1));
       coeffs_buf.reserve(std::max<int64_t>(S.s, 1));
       if (S.s) {
@@ -821,7 +882,18 @@ static void validate_sfft(const sfft_params* params, const sfft_sampler* sampler
   MR1L_REQUIRE(P.t_stop == 0 || (P.t_stop >= 2 && P.t_stop <= P.d), "t_stop must be 0 or in [2, d]");
   MR1L_REQUIRE(P.zero_anchors == 0 || P.zero_anchors == 1, "zero_anchors must be 0 or 1");
   MR1L_REQUIRE(P.fft_arith == 0 || P.fft_arith == 1, "fft_arith must be 0 (FP64) or 1 (double-float)");
-  if (!sampler->fn) {
+  if (!sampler->fn && sampler->kind == SFFT_SAMPLER_BSPLINE) {
+    const sfft_sampler& S = *sampler;
+    MR1L_REQUIRE(P.d <= kBsMaxDim, "the B-spline sampler needs d <= 64");
+    MR1L_REQUIRE(S.n_groups >= 1 && S.n_groups <= kBsMaxGroups, "n_groups must be in [1, 8]");
+    MR1L_REQUIRE(S.group_of && S.orders, "group_of and orders must not be null");
+    MR1L_REQUIRE(S.sigma == 0.0, "the B-spline sampler is noiseless (sigma must be 0)");
+    for (int i = 0; i < P.d; ++i)
+      MR1L_REQUIRE(S.group_of[i] >= -1 && S.group_of[i] < S.n_groups, "group_of entries must be in [-1, n_groups)");
+    for (int g = 0; g < S.n_groups; ++g)
+      MR1L_REQUIRE(S.orders[g] >= 2 && S.orders[g] <= kBsMaxOrder, "B-spline orders must be in [2, 8]");
+  } else if (!sampler->fn) {
+    MR1L_REQUIRE(sampler->kind == SFFT_SAMPLER_PLANTED, "unknown sampler kind");
     MR1L_REQUIRE(sampler->s >= 0, "planted s must be >= 0");
     MR1L_REQUIRE(sampler->s == 0 || (sampler->freqs && sampler->coeffs), "planted arrays are null");
     MR1L_REQUIRE(sampler->sigma >= 0.0, "sigma must be >= 0");

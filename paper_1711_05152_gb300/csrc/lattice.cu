@@ -260,6 +260,93 @@ void planted_lattice_bins(const int32_t* freqs, const cplx* coeffs, int64_t s_co
                   freqs, coeffs, s_count, d, t, anchors_dev, lat, g.off, bins, bins_stride));
 }
 
+// ---------------------------------------------------------------------------
+// Section 5.3 test function (tensor-product B-splines)
+// ---------------------------------------------------------------------------
+// N_m(x) for x in [0, 1): u = m x on knot interval q, Horner in (u - q)
+__device__ __forceinline__ double bspline_factor(const BsplineDev& S, int g, double x) {
+  const int m = S.order[g];
+  const double u = x * (double)m;
+  int q = (int)u;
+  if (q > m - 1) q = m - 1;
+  const double f = u - (double)q;
+  const double* c = S.coef[g][q];
+  double v = c[m - 1];
+  for (int k = m - 2; k >= 0; --k) v = fma(v, f, c[k]);
+  return v;
+}
+
+__device__ __forceinline__ void load_bspline(const BsplineDev* src, BsplineDev& dst) {
+  const int words = (int)(sizeof(BsplineDev) / sizeof(int));
+  for (int i = threadIdx.x; i < words; i += blockDim.x) ((int*)&dst)[i] = ((const int*)src)[i];
+  __syncthreads();
+}
+
+__global__ void bspline_lattice_kernel(const BsplineDev* Sg, int t, const double* anchors, LatticeDev lat,
+                                       const int64_t* off, cplx* y, int64_t y_stride) {
+  __shared__ BsplineDev S;
+  __shared__ double anchor_prod[kBsMaxGroups];
+  load_bspline(Sg, S);
+  const int l = blockIdx.y, h = blockIdx.z;
+  const double* xa = anchors + (int64_t)h * S.d;
+  if (threadIdx.x < S.n_groups) {  // factors of the anchored components, once per block
+    double p = 1.0;
+    for (int i = t; i < S.d; ++i)
+      if (S.group_of[i] == (int)threadIdx.x) p *= bspline_factor(S, threadIdx.x, xa[i]);
+    anchor_prod[threadIdx.x] = p;
+  }
+  __syncthreads();
+  const int64_t M = lat.M[l];
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const int64_t* z = lat.z + (int64_t)l * lat.t;
+  double prod[kBsMaxGroups];
+  for (int g = 0; g < S.n_groups; ++g) prod[g] = anchor_prod[g];
+  for (int i = 0; i < t; ++i) {
+    const int g = S.group_of[i];
+    if (g < 0) continue;
+    const double x = (double)((j * z[i]) % M) / (double)M;  // j z_i < 2^46, exact
+    prod[g] *= bspline_factor(S, g, x);
+  }
+  double f = 0.0;
+  for (int g = 0; g < S.n_groups; ++g) f += prod[g];
+  y[h * y_stride + off[l] + j] = cmake(f, 0.0);
+}
+
+void bspline_lattice(const BsplineDev* S, int t, const double* anchors_dev, int nrhs, const LatticeDev& lat,
+                     int Luse, const BlueGeom& g, int max_M, cplx* y, int64_t y_stride, cudaStream_t s) {
+  if (Luse == 0 || nrhs == 0) return;
+  MR1L_LAUNCH("bspline_lattice_kernel", s, 0, 16.0 * nrhs * g.sum_M,
+              bspline_lattice_kernel<<<dim3(cdiv(max_M, 256), Luse, nrhs), 256, 0, s>>>(S, t, anchors_dev, lat,
+                                                                                       g.off, y, y_stride));
+}
+
+__global__ void bspline_lines_kernel(const BsplineDev* Sg, int t, int K, const double* anchors, cplx* y) {
+  __shared__ BsplineDev S;
+  load_bspline(Sg, S);
+  const int i = blockIdx.y;
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= K) return;
+  const double* xa = anchors + (int64_t)i * S.d;
+  double prod[kBsMaxGroups];
+  for (int g = 0; g < S.n_groups; ++g) prod[g] = 1.0;
+  for (int c = 0; c < S.d; ++c) {
+    const int g = S.group_of[c];
+    if (g < 0) continue;
+    const double x = c == t - 1 ? (double)l / (double)K : xa[c];
+    prod[g] *= bspline_factor(S, g, x);
+  }
+  double f = 0.0;
+  for (int g = 0; g < S.n_groups; ++g) f += prod[g];
+  y[(int64_t)i * K + l] = cmake(f, 0.0);
+}
+
+void bspline_lines(const BsplineDev* S, int t, int K, const double* anchors_dev, int nlines, cplx* y,
+                   cudaStream_t s) {
+  MR1L_LAUNCH("bspline_lines_kernel", s, 0, 16.0 * nlines * K,
+              bspline_lines_kernel<<<dim3(cdiv(K, 128), nlines), 128, 0, s>>>(S, t, K, anchors_dev, y));
+}
+
 __global__ void planted_line_bins_kernel(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
                                          int K, const double* anchors, cplx* bins) {
   const int i = blockIdx.y;

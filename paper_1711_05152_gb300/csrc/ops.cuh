@@ -66,6 +66,24 @@ void planted_lines(const int32_t* freqs, const cplx* coeffs, int64_t s_count, in
                    const double* anchors_dev, int nlines, double noise_scale, uint64_t noise_seed,
                    int rep0, cplx* bins_scratch, cplx* y, cudaStream_t s);
 
+// Section 5.3 test function f(x) = sum_g prod_{t: group_of[t] = g} N_{m_g}(x_t)
+// with N_m(x) = C_m m B_m(m x): per group, the polynomial of B_m on each knot
+// interval [q, q+1) in powers of (u - q), scaled by C_m m (host-computed).
+constexpr int kBsMaxGroups = 8, kBsMaxOrder = 8, kBsMaxDim = 64;
+struct BsplineDev {
+  int d, n_groups;
+  int group_of[kBsMaxDim];
+  int order[kBsMaxGroups];
+  double coef[kBsMaxGroups][kBsMaxOrder][kBsMaxOrder];  // [g][q][power]
+};
+// y[h][off_l + j] = f(x) at node j of lattice l: x_i = (j z_{l,i} mod M_l) / M_l
+// for i < t, the anchor component anchors[h][i] for i >= t.
+void bspline_lattice(const BsplineDev* S, int t, const double* anchors_dev, int nrhs, const LatticeDev& lat,
+                     int Luse, const BlueGeom& g, int max_M, cplx* y, int64_t y_stride, cudaStream_t s);
+// y[i][l] = f(anchors[i] with component t-1 replaced by l / K).
+void bspline_lines(const BsplineDev* S, int t, int K, const double* anchors_dev, int nlines, cplx* y,
+                   cudaStream_t s);
+
 // Line detection: p~_k = (1/K) sum_l y_l e^{-2 pi i l k/K}, k = -N..N, keep
 // the (up to) cap largest keys >= threshold per line; sel[k + N] |= 1.
 void detect_lines(const cplx* y, int nlines, int N, int64_t cap, double theta2, int rel, uint8_t* sel,

@@ -81,3 +81,15 @@ def test_tile_tuner_host_controls(lib):
     P.tune_enable(False)
     P.tune_enable(True)
     assert lib.mr1l_tune_read(None, 0) == P.MR1L_E_INVAL
+
+
+@pytest.mark.parametrize("groups,orders,msg", [
+    ([[0, 1]], [9], "orders"),
+    ([[0, 1]], [1], "orders"),
+])
+def test_bspline_sampler_rejects_invalid(lib, groups, orders, msg):
+    import workloads as W
+    f = W.bspline_function(3, 4, groups, orders)
+    with pytest.raises(P.Mr1lError) as e:
+        P.sfft_dimincr(3, 4, 10, 1, 1e-12, "abs", function=f, stream=0)
+    assert e.value.code == P.MR1L_E_INVAL and msg in str(e.value)

@@ -117,6 +117,28 @@ def test_given_lattice_plan_and_uncovered():
     assert e.value.code == P.MR1L_E_NOT_RECONSTRUCTING
 
 
+@pytest.mark.parametrize("M", [2, 5, 7, 13, 2039, 2053, 4093, 4099])
+def test_small_and_boundary_primes(M):
+    """One lattice of prime size M: Bluestein lengths 3, 12, 16, 32 (the
+    one-CTA path), 4096 (its largest), 6144, 8192 and 12288 (the smallest
+    4-step lengths), with every residue class occupied (I = 0..M-1, z = 1)
+    against the direct-sum oracle, forward and both evaluation modes."""
+    I = np.arange(M).reshape(-1, 1)
+    pl = P.plan(I, [M], [[1]], strict=True)
+    ml = lattice.MultiLattice([M], [np.array([1])], [np.ones(M, dtype=bool)], True, 1)
+    rng = np.random.default_rng(M)
+    y = rng.standard_normal((2, M)) + 1j * rng.standard_normal((2, M))
+    c = rng.standard_normal((2, M)) + 1j * rng.standard_normal((2, M))
+    got = pl.reconstruct(torch.from_numpy(y).cuda()).cpu().numpy()
+    ge = pl.evaluate(torch.from_numpy(c).cuda(), P.MR1L_EVAL).cpu().numpy()
+    ga = pl.evaluate(torch.from_numpy(c).cuda(), P.MR1L_ADJOINT).cpu().numpy()
+    for h in range(2):
+        want, _ = lattice.reconstruct(I, ml, [y[h]], "direct")
+        assert _normwise(got[h], want) < RTOL
+        assert _normwise(ge[h], np.concatenate(lattice.evaluate(I, ml, c[h], "eval", "direct"))) < RTOL
+        assert _normwise(ga[h], np.concatenate(lattice.evaluate(I, ml, c[h], "adjoint", "direct"))) < RTOL
+
+
 @pytest.mark.parametrize("M", [1_300_021, 2_000_003, 3_000_017, 8_000_009])
 def test_large_single_lattice_4step(M):
     """One lattice per case, chosen so that the Bluestein length is 3 * 2^20,
@@ -199,6 +221,16 @@ def test_sfft_zero_anchors_parity(seed):
         _assert_sfft_equal(out, ref)
         if snr is None:
             np.testing.assert_array_equal(out.freqs, sig.freqs.astype(np.int64))
+
+
+def test_sfft_smallest_box():
+    """N = 1 (frequencies in {-1, 0, 1}^6, K = 3 line samples): half of the
+    box planted."""
+    sig = W.planted_signal(6, 1, 360, seed=3, model="u1_10")
+    out = P.sfft_dimincr(6, 1, 360, 2, 1e-12, "rel", seed=3, freqs=sig.freqs, coeffs=sig.coeffs)
+    ref = sfft.sfft(sig, 360, 360, 2, 10, 1e-12, "rel", seed=3)
+    _assert_sfft_equal(out, ref)
+    np.testing.assert_array_equal(out.freqs, sig.freqs.astype(np.int64))
 
 
 def test_sfft_batched_reps_identical():

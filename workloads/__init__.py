@@ -19,6 +19,9 @@ import math
 import numpy as np
 
 __all__ = [
+    "BsplineFunction",
+    "bspline_function",
+    "paper_bspline",
     "PlantedSignal",
     "planted_signal",
     "noise_sigma",
@@ -162,3 +165,32 @@ def diff_problem(n_freq: int, d: int, N: int, nrhs: int, seed: int):
 def complex_normal(rng: np.random.Generator, shape) -> np.ndarray:
     return ((rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2.0)).astype(
         np.complex128)
+
+
+@dataclasses.dataclass
+class BsplineFunction:
+    """The description (no evaluation) of a Section 5.3 test function
+    f(x) = sum_g prod_{t in groups[g]} N_{orders[g]}(x_t): disjoint 0-based
+    dimension groups and one B-spline order per group; N is the search box
+    [-N, N]^d of the sparse FFT run; noiseless."""
+
+    d: int
+    N: int
+    groups: list
+    orders: list
+    sigma: float = 0.0
+
+
+def bspline_function(d: int, N: int, groups, orders) -> BsplineFunction:
+    groups = [sorted(int(t) for t in g) for g in groups]
+    flat = [t for g in groups for t in g]
+    if len(set(flat)) != len(flat) or any(t < 0 or t >= d for t in flat) or len(groups) != len(orders):
+        raise ValueError("groups must be disjoint subsets of range(d), one order per group")
+    return BsplineFunction(d=d, N=N, groups=groups, orders=[int(m) for m in orders])
+
+
+def paper_bspline(N: int) -> BsplineFunction:
+    """Section 5.3: f(x) = N_2(x1) N_2(x3) N_2(x8) + N_4(x2) N_4(x5) N_4(x6) N_4(x10)
+    + N_6(x4) N_6(x7) N_6(x9) on T^10."""
+    return bspline_function(10, N, [[0, 2, 7], [1, 4, 5, 9], [3, 6, 8]], [2, 4, 6])
+
