@@ -568,9 +568,10 @@ struct SfftRun {
   DevBuf<cplx> line_y, line_bins;
   std::vector<cudaEvent_t> ev;
   std::vector<double> final_coeffs;
-  // measurement noise: drawn on a side stream while the main stream runs the
-  // sampler's inverse transform (FP64 noise work overlaps the FFT work), then
-  // added to the samples by the reconstruct pass as it loads them
+  // measurement noise: drawn on a side stream (its arithmetic runs on the FP32
+  // pipes) while the main stream runs the sampler's inverse transform on the
+  // FP64 pipe, then added to the samples by the reconstruct pass as it loads
+  // them
   cudaStream_t side = nullptr;
   cudaEvent_t ev_free = nullptr, ev_noise = nullptr;
   DevBuf<cplx> noise;
