@@ -364,12 +364,27 @@ def run_ours(args):
     h2d = sum(sig.freqs.size * 4 + sig.coeffs.size * 16 for sig, _ in wl.items)
     d2h = int(sum(o.freqs.size * 4 + o.coeffs.size * 16 for o in outs))
 
+    # The batched form of the 256-signal workload runs 16 streams at once, so a
+    # kernel's events also cover time its CTAs wait behind other streams; its
+    # per-kernel times come from one extra, untimed solve of the single-stream
+    # form instead.
+    prof_src = "the batched timed region"
+    prof = bat["prof"] or {}
+    if args.workload == "batch256":
+        torch.cuda.synchronize()
+        P.prof_reset()
+        P.prof_enable(True)
+        wl.solve(False)
+        torch.cuda.synchronize()
+        P.prof_enable(False)
+        prof = P.prof_read()
+        prof_src = "one extra solve of the single-stream form (the batched form overlaps 16 streams)"
+
     if rank != 0:
         return 0
 
     last = bat["last"]
     value = bat["detected"] / (bat["ms"] / 1e3)
-    prof = bat["prof"] or {}
     total_prof_ms = sum(v["ms"] for v in prof.values()) or 1.0
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
     peaks, peak_src = _peaks()
@@ -389,13 +404,15 @@ def run_ours(args):
             roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                         "peak_source": "FP64 pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (derived)",
-                        "share_of_kernel_time": dom["ms"] / total_prof_ms, "launches": dom["launches"]}
+                        "share_of_kernel_time": dom["ms"] / total_prof_ms, "launches": dom["launches"],
+                        "timed_in": prof_src}
         else:
             achieved = dom["bytes"] / dom["launches"] / (per_launch_ms * 1e-3) / 1e9
             pk = peaks.get("hbm_gbs", 6800.0)
             roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": pk, "unit": "GB/s",
                         "frac": achieved / pk, "traffic": traffic, "peak_source": peak_src,
-                        "share_of_kernel_time": dom["ms"] / total_prof_ms, "launches": dom["launches"]}
+                        "share_of_kernel_time": dom["ms"] / total_prof_ms, "launches": dom["launches"],
+                        "timed_in": prof_src}
 
     # lattice transform (Algorithm 2): Bluestein reconstruct passes + gather
     recon = [k for k in prof if k.endswith("_recon") or k == "gather_kernel"]

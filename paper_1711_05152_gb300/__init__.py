@@ -380,10 +380,12 @@ def _convert(res: sfft_result) -> SfftOutput:
 
 
 def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[SfftOutput]:
-    """Algorithm 3 on many independent planted problems at once.  Each problem
-    is a dict with d, N, s, r, theta, theta_mode, seed, freqs, coeffs (host
-    arrays, or contiguous int32 / complex128 CUDA tensors) and optionally
-    sigma, s_local, b, noise_seed, batch_reps, fft, zero_anchors."""
+    """Algorithm 3 on many independent problems at once.  Each problem is a
+    dict with d, N, s, r, theta, theta_mode, seed and either freqs, coeffs
+    (a planted polynomial: host arrays, or contiguous int32 / complex128 CUDA
+    tensors) or function (the Section 5.3 B-spline function, see
+    sfft_dimincr), and optionally sigma, s_local, b, noise_seed, batch_reps,
+    fft, zero_anchors."""
     n = len(problems)
     params = (sfft_params * max(n, 1))()
     samps = (sfft_sampler * max(n, 1))()
@@ -396,6 +398,9 @@ def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[Sfft
                                 seed=q["seed"], batch_reps=1 if q.get("batch_reps", True) else 0,
                                 fft_arith=1 if q.get("fft", "f64") == "df" else 0,
                                 zero_anchors=1 if q.get("zero_anchors", False) else 0)
+        if q.get("function") is not None:
+            samps[i] = _bspline_sampler(d, q["function"], keep)
+            continue
         if getattr(q["freqs"], "is_cuda", False):
             f, c = q["freqs"], q["coeffs"]
             keep += [f, c]

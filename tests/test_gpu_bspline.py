@@ -91,3 +91,21 @@ def test_paper_function_full_run():
     assert err < 2e-2, err
     assert np.max(np.abs(out.coeffs - sig.coeff(out.freqs))) < 1e-3
     assert 0.5 * 62_671_623 < out.samples < 1.5 * 62_671_623
+
+
+def test_bspline_in_a_batch_with_planted_problems():
+    """sfft_dimincr_batch mixes function and planted problems; each result
+    equals the one of its own sfft_dimincr call."""
+    desc = W.bspline_function(4, 6, [[0, 2], [1, 3]], [2, 6])
+    full = 13 ** 4
+    sig, p = W.workload("tiny_d3", 2)
+    probs = [dict(d=4, N=6, s=full, s_local=full, r=2, theta=1e-5, theta_mode="abs", seed=5, function=desc,
+                  batch_reps=False),
+             dict(d=sig.d, N=sig.N, s=p["s"], s_local=p["s_local"], r=p["r"], b=p["b"], theta=p["theta"],
+                  theta_mode=p["theta_mode"], seed=2, freqs=sig.freqs, coeffs=sig.coeffs, sigma=sig.sigma,
+                  batch_reps=False)]
+    outs = P.sfft_dimincr_batch(probs, concurrency=2)
+    one = P.sfft_dimincr(4, 6, full, 2, 1e-5, "abs", seed=5, function=desc)
+    np.testing.assert_array_equal(outs[0].freqs, one.freqs)
+    np.testing.assert_array_equal(outs[0].coeffs, one.coeffs)
+    np.testing.assert_array_equal(outs[1].freqs, sig.freqs.astype(np.int64))
