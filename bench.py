@@ -493,12 +493,12 @@ def _paper_rows(name):
     return rows
 
 
-def _run_stats(problems, sigs, fft):
+def _run_stats(problems, sigs, fft, concurrency=16):
     """Detected-set and coefficient statistics of a list of planted problems."""
     import paper_1711_05152_gb300 as P
     for q in problems:
         q["fft"] = fft
-    outs = P.sfft_dimincr_batch(problems, concurrency=16)
+    outs = P.sfft_dimincr_batch(problems, concurrency=concurrency)
     samples, correct, success, err = [], [], [], []
     for sig, o in zip(sigs, outs):
         truth = {tuple(f): c for f, c in zip(sig.freqs.astype(int).tolist(), sig.coeffs)}
@@ -560,7 +560,8 @@ def run_paper_table(args):
             sigs = [W.planted_signal(d, 32, supp, seed=base + i, model="box") for i in range(reps)]
             probs = [dict(d=d, N=32, s=supp, s_local=supp, r=1, b=10, theta=1e-12, theta_mode="abs",
                           seed=base + i, freqs=g.freqs, coeffs=g.coeffs) for i, g in enumerate(sigs)]
-            st = _run_stats(probs, sigs, args.fft)
+            # |supp| = 1e5 solves hold about 25 GB of device buffers each: two at a time
+            st = _run_stats(probs, sigs, args.fft, concurrency=16 if supp < 100000 else 2)
             print(json.dumps({"paper_table": "5.1", "d": d, "supp": supp, "reps": reps, "fft": args.fft, **st,
                               "paper": {"max_samples": int(pmax), "max_rel_l2": perr},
                               "samples_over_paper": st["max_samples"] / pmax,

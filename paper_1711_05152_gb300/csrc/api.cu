@@ -233,7 +233,7 @@ struct LatticeWork {
       sumM += Mh[l];
     }
     const int P = blue_length(2 * (int64_t)maxM - 1);
-    MR1L_REQUIRE(P > 0, "lattice size too large for the Bluestein FFT (2 M - 1 > 2^24)");
+    MR1L_REQUIRE(P > 0, "lattice size too large for the Bluestein FFT (2 M - 1 > 2^25)");
     geom = BlueGeom{};
     blue_split(geom, P);
     geom.L = Luse;

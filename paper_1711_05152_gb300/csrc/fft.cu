@@ -213,7 +213,7 @@ __device__ __forceinline__ void stockham_stage(typename O::V* s, int n, int Ns, 
 // Twiddles exp(-2 pi i e / n) of a sub-FFT length n (2^a or 3 * 2^a).
 template <class T>
 __device__ __forceinline__ const T* twiddles_of(const T* twn, int n) {
-  return (n & (n - 1)) == 0 ? twn + n : twn + 8192 + n - 3;
+  return (n & (n - 1)) == 0 ? twn + n : twn + kSmallTwPow2 + n - 3;
 }
 
 // Full in-smem FFT of length n = 2^a or 3 * 2^a: radix-8 stages, one radix-4
@@ -362,15 +362,18 @@ __host__ __device__ __forceinline__ int row_tile(int P2, int P1, int tile) {
 // Register budget of the 4-step kernels: the double-float passes wait on
 // memory more than on arithmetic, so they are held to 64 registers (two
 // 512-thread or four 256-thread CTAs per SM; a few bytes spill) for the
-// occupancy; the FP64 passes keep what the compiler picks (up to 128).
+// occupancy; the FP64 passes keep what the compiler picks (up to 128).  The
+// largest lengths (2^25, 3 * 2^23) have single columns of 6144 or rows of
+// 8192 elements, one CTA of up to 1024 threads each (NT = 1024: at most 64
+// registers, so the FP64 kernels spill a little there).
 template <class O>
 struct MinBlocks {
   static constexpr int value = std::is_same<O, OpsDF>::value ? 2 : 1;
 };
 
 // Pass 1: columns, forward, with the 4-step twiddle.
-template <int MODE, class O>
-__global__ void __launch_bounds__(512, MinBlocks<O>::value) blue_col_fwd_kernel(BlueGeom g, BlueIO io) {
+template <int MODE, class O, int NT = 512>
+__global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_col_fwd_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -467,8 +470,8 @@ __global__ void __launch_bounds__(512, MinBlocks<O>::value) blue_col_fwd_kernel(
 
 // Pass 2: rows.  FILTER: forward FFT scaled by 1/P into Bh.  Otherwise forward
 // FFT, times Bh, inverse FFT, times conj(w_P^(n2 k1)).
-template <bool FILTER, class O>
-__global__ void __launch_bounds__(512, MinBlocks<O>::value) blue_row_kernel(BlueGeom g, BlueIO io) {
+template <bool FILTER, class O, int NT = 512>
+__global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_row_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -499,8 +502,8 @@ __global__ void __launch_bounds__(512, MinBlocks<O>::value) blue_row_kernel(Blue
 }
 
 // Pass 3: columns, inverse; natural-order output n = n1 P2 + n2 for n < M.
-template <int MODE, class O>
-__global__ void __launch_bounds__(512, MinBlocks<O>::value) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
+template <int MODE, class O, int NT = 512>
+__global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -539,11 +542,11 @@ __global__ void small_twiddle_kernel(cplx* tw) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < 2 || i >= kSmallTw) return;
   int n, e;
-  if (i < 8192) {  // n = 2^a at [n, 2n)
+  if (i < kSmallTwPow2) {  // n = 2^a at [n, 2n)
     n = 1 << (31 - __clz(i));
     e = i - n;
-  } else {         // n = 3 * 2^a at [8192 + n - 3, 8192 + 2n - 3)
-    int j = i - 8192 + 3;              // in [n, 2n) for n = 3 * 2^a
+  } else {                 // n = 3 * 2^a at [kSmallTwPow2 + n - 3, kSmallTwPow2 + 2n - 3)
+    int j = i - kSmallTwPow2 + 3;      // in [n, 2n) for n = 3 * 2^a
     int a = 31 - __clz(j / 3);
     n = 3 << a;
     e = j - n;
@@ -555,8 +558,9 @@ __global__ void small_twiddle_kernel(cplx* tw) {
 
 // Chirp w[n] = exp(-pi i q / M), q = n^2 mod 2M (exact), as the product of two
 // tabulated factors exp(-pi i (q >> 12) 4096 / M) * exp(-pi i (q & 4095) / M):
-// per-lattice tables of kChirpLo entries each (2M <= 2^24 leaves at most 4096
-// high parts), filled by sincospi of exactly reduced arguments, so that a
+// per-lattice tables of kChirpLo and kChirpSeedLen - kChirpLo entries (2M <=
+// 2^25 leaves at most 8192 high parts), filled by sincospi of exactly reduced
+// arguments, so that a
 // sample costs one complex product instead of a sine and a cosine.
 constexpr int kChirpLo = 4096;
 
@@ -683,8 +687,8 @@ int blue_length(int64_t n) {
   while (p3 < n) p3 <<= 1;
   if (p2 < 4) p2 = 4;
   int64_t best = 0;
-  if (p2 <= (int64_t(1) << 24)) best = p2;
-  if (p3 <= 3 * (int64_t(1) << 22) && (best == 0 || p3 < best)) best = p3;
+  if (p2 <= (int64_t(1) << 25)) best = p2;
+  if (p3 <= 3 * (int64_t(1) << 23) && (best == 0 || p3 < best)) best = p3;
   return (int)best;
 }
 
@@ -752,31 +756,57 @@ static void launch_passes(const BlueGeom& g, const BlueIO& io, int ntrans, cudaS
   size_t smem_r = (size_t)RB * g.P2 * sizeof(cplx);
   dim3 gc(g.P2 / CB, ntrans), gr(g.P1 / RB, ntrans);
   const double P1 = g.P1, P2 = g.P2;
+  const int tc = threads_for(g.P1 * CB), tr = threads_for(RB * g.P2);
+  MR1L_REQUIRE(tc <= 1024 && tr <= 1024, "4-step tile larger than one CTA");
   if (ev) MR1L_CUDA(cudaEventRecord(ev[0], s));
-  set_smem(blue_col_fwd_kernel<MODE, O>, smem_c);
-  MR1L_LAUNCH((pass_name<MODE, O>("col_fwd", nm)), s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM,
-              nr * sumM * cb * 2 + ntrans * P * cb,
-              blue_col_fwd_kernel<MODE, O><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
+  if (tc <= 512) {
+    set_smem(blue_col_fwd_kernel<MODE, O>, smem_c);
+    MR1L_LAUNCH((pass_name<MODE, O>("col_fwd", nm)), s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM,
+                nr * sumM * cb * 2 + ntrans * P * cb, blue_col_fwd_kernel<MODE, O><<<gc, tc, smem_c, s>>>(g, io));
+  } else {
+    set_smem(blue_col_fwd_kernel<MODE, O, 1024>, smem_c);
+    MR1L_LAUNCH((pass_name<MODE, O>("col_fwd", nm)), s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM,
+                nr * sumM * cb * 2 + ntrans * P * cb,
+                blue_col_fwd_kernel<MODE, O, 1024><<<gc, tc, smem_c, s>>>(g, io));
+  }
   if (ev) MR1L_CUDA(cudaEventRecord(ev[1], s));
   if (MODE == kModeFilter) {
-    set_smem(blue_row_kernel<true, O>, smem_r);
-    MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
-                blue_row_kernel<true, O><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
+    if (tr <= 512) {
+      set_smem(blue_row_kernel<true, O>, smem_r);
+      MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
+                  blue_row_kernel<true, O><<<gr, tr, smem_r, s>>>(g, io));
+    } else {
+      set_smem(blue_row_kernel<true, O, 1024>, smem_r);
+      MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
+                  blue_row_kernel<true, O, 1024><<<gr, tr, smem_r, s>>>(g, io));
+    }
     if (ev) {
       MR1L_CUDA(cudaEventRecord(ev[2], s));
       MR1L_CUDA(cudaEventRecord(ev[3], s));
     }
     return;
   }
-  set_smem(blue_row_kernel<false, O>, smem_r);
-  MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
-              blue_row_kernel<false, O><<<gr, threads_for(RB * g.P2), smem_r, s>>>(g, io));
+  if (tr <= 512) {
+    set_smem(blue_row_kernel<false, O>, smem_r);
+    MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
+                blue_row_kernel<false, O><<<gr, tr, smem_r, s>>>(g, io));
+  } else {
+    set_smem(blue_row_kernel<false, O, 1024>, smem_r);
+    MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
+                blue_row_kernel<false, O, 1024><<<gr, tr, smem_r, s>>>(g, io));
+  }
   if (ev) MR1L_CUDA(cudaEventRecord(ev[2], s));
-  set_smem(blue_col_inv_kernel<MODE, O>, smem_c);
-  MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s,
-              ntrans * P2 * fft_flops(P1) + (MODE == kModeEval ? nr * 6 * sumM : 0.0),
-              ntrans * P * cb + nr * sumM * cb * (MODE == kModeEval ? 2 : 1),
-              blue_col_inv_kernel<MODE, O><<<gc, threads_for(g.P1 * CB), smem_c, s>>>(g, io));
+  const double fl_ci = ntrans * P2 * fft_flops(P1) + (MODE == kModeEval ? nr * 6 * sumM : 0.0);
+  const double by_ci = ntrans * P * cb + nr * sumM * cb * (MODE == kModeEval ? 2 : 1);
+  if (tc <= 512) {
+    set_smem(blue_col_inv_kernel<MODE, O>, smem_c);
+    MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s, fl_ci, by_ci,
+                blue_col_inv_kernel<MODE, O><<<gc, tc, smem_c, s>>>(g, io));
+  } else {
+    set_smem(blue_col_inv_kernel<MODE, O, 1024>, smem_c);
+    MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s, fl_ci, by_ci,
+                blue_col_inv_kernel<MODE, O, 1024><<<gc, tc, smem_c, s>>>(g, io));
+  }
   if (ev) MR1L_CUDA(cudaEventRecord(ev[3], s));
 }
 

@@ -27,8 +27,8 @@ struct BlueGeom {
   const cplx* ws;       // device [sum M]: chirp / M
   cplx* Bh;             // device [L][P]: filter spectrum FFT_P(b) / P (pass order)
   const cplx* tw;       // device [P]: exp(-2 pi i e / P)
-  const cplx* twn;      // device [kSmallTw]: exp(-2 pi i e / n), n = 2^a <= 4096 at offset n,
-                        //   n = 3 * 2^a <= 6144 at offset 8192 + n - 3
+  const cplx* twn;      // device [kSmallTw]: exp(-2 pi i e / n), n = 2^a <= 8192 at offset n,
+                        //   n = 3 * 2^a <= 6144 at offset kSmallTwPow2 + n - 3
   int64_t sum_M;        // host: sum of the L lattice sizes (for launch accounting)
   // double-float arithmetic (df != 0): the same tables as hi/lo FP32 pairs
   // (float4 = re.hi, re.lo, im.hi, im.lo); Bh then holds float4 data
@@ -61,7 +61,8 @@ struct BlueIO {
 };
 
 constexpr int kSmallMax = 4096;  // P <= 4096: one CTA holds the whole transform
-constexpr int kSmallTw = 8192 + 12288;
+constexpr int kSmallTwPow2 = 16384;  // power-of-two sub-FFT lengths up to 8192
+constexpr int kSmallTw = kSmallTwPow2 + 12288;
 
 // Device-resident twiddle tables, cached per (device, P).
 const cplx* twiddle_table(int P, cudaStream_t s);
@@ -72,7 +73,7 @@ const float4* small_twiddles_df(cudaStream_t s);
 void to_double_float(const cplx* src, float4* dst, int64_t n, cudaStream_t s);
 const cplx* small_twiddles(cudaStream_t s);
 
-// The smallest supported convolution length P >= n (2^k <= 2^24 or 3 * 2^k <= 3 * 2^22);
+// The smallest supported convolution length P >= n (2^k <= 2^25 or 3 * 2^k <= 3 * 2^23);
 // 0 if there is none.
 int blue_length(int64_t n);
 
@@ -97,7 +98,7 @@ std::string tune_json();
 
 // Chirp tables w and ws for every lattice (w[n] = exp(-pi i (n^2 mod 2M)/M)).
 // seed: device scratch of g.L * kChirpSeedLen complex (per-lattice factor tables).
-constexpr int kChirpSeedLen = 8192;
+constexpr int kChirpSeedLen = 4096 + 8192;
 void chirp_tables(const BlueGeom& g, int64_t max_M, cplx* seed, cudaStream_t s);
 
 }  // namespace mr1l

@@ -54,7 +54,7 @@ def test_df_reconstruct_and_adjoint(n, t, N):
         assert _normwise(gotb[h], wantb) < RTOL
 
 
-@pytest.mark.parametrize("M", [1_300_021, 3_000_017])
+@pytest.mark.parametrize("M", [1_300_021, 3_000_017, 16_700_003])
 def test_df_large_lattice(M):
     I = np.arange(-30000, 30000).reshape(-1, 1)
     pl = P.plan(I, [M], [[7919]], fft="df")

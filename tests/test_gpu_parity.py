@@ -139,11 +139,12 @@ def test_small_and_boundary_primes(M):
         assert _normwise(ga[h], np.concatenate(lattice.evaluate(I, ml, c[h], "adjoint", "direct"))) < RTOL
 
 
-@pytest.mark.parametrize("M", [1_300_021, 2_000_003, 3_000_017, 8_000_009])
+@pytest.mark.parametrize("M", [1_300_021, 2_000_003, 3_000_017, 8_000_009, 10_000_019, 16_700_003])
 def test_large_single_lattice_4step(M):
     """One lattice per case, chosen so that the Bluestein length is 3 * 2^20,
-    2^22, 3 * 2^21 (one-column tiles) and 2^24 (the largest), against numpy's
-    FFT."""
+    2^22, 3 * 2^21 (one-column tiles), 2^24, 3 * 2^23 (single 6144-element
+    columns, 768-thread CTAs) and 2^25 (the largest: single 8192-element rows,
+    1024-thread CTAs), against numpy's FFT."""
     assert lattice.is_prime(M)
     I = np.arange(-30000, 30000).reshape(-1, 1)
     pl = P.plan(I, [M], [[7919]])
