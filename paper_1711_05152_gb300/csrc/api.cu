@@ -939,6 +939,7 @@ extern "C" int sfft_dimincr_batch(const sfft_params* params, const sfft_sampler*
     // twiddle tables are built under a lock by whichever worker needs them first
     const int workers = std::min(concurrency, std::max(count, 1));
     std::atomic<int> next{0};
+    std::vector<std::string> why(count);  // each failed problem's message (workers' errors are thread-local)
     auto worker = [&]() {
       cudaSetDevice(dev);
       cudaStream_t s = nullptr;
@@ -951,6 +952,7 @@ extern "C" int sfft_dimincr_batch(const sfft_params* params, const sfft_sampler*
           continue;
         }
         status[i] = guarded([&] { out[i] = run_one(params[i], samplers[i], s); });
+        if (status[i] != MR1L_OK) why[i] = tl_msg;
       }
       if (s) cudaStreamDestroy(s);
     };
@@ -958,7 +960,7 @@ extern "C" int sfft_dimincr_batch(const sfft_params* params, const sfft_sampler*
     for (int w = 0; w < workers; ++w) pool.emplace_back(worker);
     for (auto& th : pool) th.join();
     for (int i = 0; i < count; ++i)
-      if (status[i] != MR1L_OK) throw Error(status[i], "problem " + std::to_string(i) + " failed");
+      if (status[i] != MR1L_OK) throw Error(status[i], "problem " + std::to_string(i) + " failed: " + why[i]);
   });
 }
 
