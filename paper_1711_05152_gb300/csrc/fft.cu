@@ -468,8 +468,125 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Row tiles with fused sources and sinks.  A row pass transforms rows of
+// length P2 = 2^b (b >= 6) element-fastest across threads.  Its first stage
+// reads the work tile straight from global memory, the filter product rides on
+// the last forward stage, and the twiddle product and the store ride on the
+// last inverse stage, which saves three passes over shared memory and their
+// barriers.
+// ---------------------------------------------------------------------------
+template <class O>
+struct RowSmem {
+  typename O::V* s;
+  int P2;
+  __device__ __forceinline__ typename O::V ld(int b, int i) const { return s[b * P2 + i]; }
+  __device__ __forceinline__ void st(int b, int i, typename O::V v) const { s[b * P2 + i] = O::norm(v); }
+};
+template <class O>
+struct RowLoad {  // the work tile in global memory
+  const typename O::V* p;
+  int P2;
+  __device__ __forceinline__ typename O::V ld(int b, int i) const { return p[b * P2 + i]; }
+};
+template <class O>
+struct RowTimesFilter {  // shared memory <- v * filter spectrum
+  typename O::V* s;
+  const typename O::V* Bh;
+  int P2;
+  __device__ __forceinline__ void st(int b, int i, typename O::V v) const {
+    s[b * P2 + i] = O::mul(v, Bh[b * P2 + i]);
+  }
+};
+template <class O>
+struct RowStoreTwiddled {  // work tile <- v conj(w_P^(n2 k1))
+  typename O::V* p;
+  const typename O::V* tw;
+  int P2, k1_0;
+  __device__ __forceinline__ void st(int b, int i, typename O::V v) const {
+    p[b * P2 + i] = O::mulc(v, tw[i * (k1_0 + b)]);
+  }
+};
+template <class O>
+struct RowStoreScaled {  // filter spectrum <- v / P
+  typename O::V* p;
+  int P2;
+  double sc;
+  float sh, sl;
+  __device__ __forceinline__ void st(int b, int i, typename O::V v) const { p[b * P2 + i] = O::scalec(v, sc, sh, sl); }
+};
+
+// One radix-R Stockham stage over nrows rows of length n, element-fastest;
+// element i of row b is read as src.ld(b, i) and written as dst.st(b, i, v).
+template <int R, bool INV, class O, class Src, class Dst>
+__device__ __forceinline__ void row_stage(int n, int Ns, int nrows, const typename O::V* twn_n, const Src& src,
+                                          const Dst& dst) {
+  typedef typename O::V V;
+  constexpr int CNT = (8 + R - 1) / R;
+  const int nb = n / R;
+  const int total = nrows * nb;
+  V v[CNT][R];
+  int rb[CNT], ob[CNT];
+  bool act[CNT];
+#pragma unroll
+  for (int c = 0; c < CNT; ++c) {
+    const int idx = threadIdx.x + c * blockDim.x;
+    act[c] = idx < total;
+    const int b = idx / nb, j = idx - b * nb, k = j % Ns;
+    rb[c] = b;
+    ob[c] = (j - k) * R + k;
+    if (act[c]) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[c][r] = src.ld(b, j + r * nb);
+      if (Ns > 1) {
+        const int step = k * (n / (Ns * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const V w = twn_n[r * step];
+          v[c][r] = INV ? O::mulc(v[c][r], w) : O::mul(v[c][r], w);
+        }
+      }
+      RegDft<R, INV, O>::run(v[c]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < CNT; ++c) {
+    if (act[c]) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst.st(rb[c], ob[c] + r * Ns, v[c][r]);
+    }
+  }
+  __syncthreads();
+}
+
+// FFT of nrows rows of length P2 = 2^b (b >= 6): radix-8 stages, then one
+// radix-4 or radix-2 stage; input through src, output through dst, the stages
+// in between in the shared-memory tile sm.
+template <bool INV, class O, class Src, class Dst>
+__device__ __forceinline__ void row_fft_io(typename O::V* sm, int P2, int nrows, const typename O::V* twn,
+                                           const Src& src, const Dst& dst) {
+  const typename O::V* tw = twiddles_of(twn, P2);
+  const RowSmem<O> smio{sm, P2};
+  const int b = 31 - __clz(P2), n8 = b / 3, tail = b % 3;
+  row_stage<8, INV, O>(P2, 1, nrows, tw, src, smio);
+  int Ns = 8;
+  const int mid = n8 - 1 - (tail == 0 ? 1 : 0);
+  for (int i = 0; i < mid; ++i) {
+    row_stage<8, INV, O>(P2, Ns, nrows, tw, smio, smio);
+    Ns <<= 3;
+  }
+  if (tail == 0)
+    row_stage<8, INV, O>(P2, Ns, nrows, tw, smio, dst);
+  else if (tail == 2)
+    row_stage<4, INV, O>(P2, Ns, nrows, tw, smio, dst);
+  else
+    row_stage<2, INV, O>(P2, Ns, nrows, tw, smio, dst);
+}
+
 // Pass 2: rows.  FILTER: forward FFT scaled by 1/P into Bh.  Otherwise forward
-// FFT, times Bh, inverse FFT, times conj(w_P^(n2 k1)).
+// FFT, times Bh, inverse FFT, times conj(w_P^(n2 k1)), with the loads and
+// stores fused into the first and last stages (row_fft_io).
 template <bool FILTER, class O, int NT = 512>
 __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_row_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
@@ -480,25 +597,17 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
   const int P = g.P, P2 = g.P2, RB = row_tile(P2, g.P1, g.rtile);
   const int k1_0 = blockIdx.x * RB;
   V* work = (V*)io.work + (int64_t)gi * P + (int64_t)k1_0 * P2;
-  for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = work[e];
-  __syncthreads();
-  smem_fft<false, false, O>(sm, P2, RB, P2, 1, Tab<O>::twn(g));
   V* Bh = Tab<O>::Bh(g) + (int64_t)l * P + (int64_t)k1_0 * P2;
+  const RowLoad<O> src{work, P2};
   if (FILTER) {
     const double sc = 1.0 / (double)P;
     const float sh = __double2float_rn(sc), sl = __double2float_rn(sc - (double)sh);
-    for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) Bh[e] = O::scalec(sm[e], sc, sh, sl);
+    row_fft_io<false, O>(sm, P2, RB, Tab<O>::twn(g), src, RowStoreScaled<O>{Bh, P2, sc, sh, sl});
     return;
   }
-  for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) sm[e] = O::mul(sm[e], Bh[e]);
-  __syncthreads();
-  smem_fft<true, false, O>(sm, P2, RB, P2, 1, Tab<O>::twn(g));
-  const V* tw = Tab<O>::tw(g);
-  for (int e = threadIdx.x; e < RB * P2; e += blockDim.x) {
-    int b = e / P2, n2 = e - b * P2;
-    int k1 = k1_0 + b;
-    work[e] = O::mulc(sm[e], tw[n2 * k1]);
-  }
+  row_fft_io<false, O>(sm, P2, RB, Tab<O>::twn(g), src, RowTimesFilter<O>{sm, Bh, P2});
+  row_fft_io<true, O>(sm, P2, RB, Tab<O>::twn(g), RowSmem<O>{sm, P2},
+                      RowStoreTwiddled<O>{work, Tab<O>::tw(g), P2, k1_0});
 }
 
 // Pass 3: columns, inverse; natural-order output n = n1 P2 + n2 for n < M.
