@@ -292,6 +292,19 @@ int sfft_dimincr(const sfft_params* params, const sfft_sampler* sampler, void* s
 void sfft_free(sfft_result* res);
 
 /*
+ * sfft_theorem_params - the parameters of the theorem in Section 4 that
+ * bounds the failure probability of Algorithm 3 by eps (0 < eps < 1) for a
+ * polynomial with `supp` non-zero coefficients in d dimensions:
+ *   r = ceil(2 supp (ln 3 + ln d + ln supp - ln eps))   detection iterations,
+ *   b = ceil((ln 3 + ln d - ln eps) / ln 2)            lattice searches.
+ * (Natural logarithms.)  The theorem also asks for an absolute threshold
+ * delta <= min |c| / 3 and s >= supp.  These r are far above what the
+ * experiments need (r = 1..5), so they are a worst-case setting.  Host only.
+ * Returns MR1L_E_INVAL for d < 1, supp < 1 or eps outside (0, 1).
+ */
+int sfft_theorem_params(int d, int64_t supp, double eps, int64_t* r, int* b);
+
+/*
  * sfft_dimincr_batch - Algorithm 3 on `count` independent problems
  * (params[i], samplers[i]; uneven d, N, s allowed).  Up to `concurrency`
  * problems run at once, each on its own non-blocking CUDA stream driven by its

@@ -43,7 +43,7 @@ EXPORTS = [
     "mr1l_last_error", "mr1l_version", "mr1l_plan", "mr1l_plan_search", "mr1l_plan_info",
     "mr1l_plan_masks", "mr1l_destroy", "mr1l_reconstruct", "mr1l_evaluate", "sfft_dimincr",
     "sfft_free", "sfft_dimincr_batch", "mr1l_reconstruct_noalloc", "mr1l_lattice_noise", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
-    "mr1l_tune_enable", "mr1l_tune_reset", "mr1l_tune_read",
+    "mr1l_tune_enable", "mr1l_tune_reset", "mr1l_tune_read", "sfft_theorem_params",
 ]
 
 
@@ -143,6 +143,7 @@ def lib() -> C.CDLL:
     L.mr1l_prof_launches.argtypes = []
     L.mr1l_prof_launches.restype = C.c_longlong
     L.mr1l_prof_read.argtypes = [C.c_char_p, C.c_size_t]
+    L.sfft_theorem_params.argtypes = [C.c_int, C.c_int64, C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_int)]
     L.mr1l_tune_enable.argtypes = [C.c_int]
     L.mr1l_tune_reset.argtypes = []
     L.mr1l_tune_read.argtypes = [C.c_char_p, C.c_size_t]
@@ -472,3 +473,11 @@ def tune_read() -> list:
     buf = C.create_string_buffer(1 << 16)
     _check(lib().mr1l_tune_read(buf, 1 << 16))
     return json.loads(buf.value.decode())
+
+
+def theorem_params(d: int, supp: int, eps: float) -> tuple[int, int]:
+    """(r, b) of the Section 4 theorem for failure probability eps (see sfft_theorem_params)."""
+    r, b = C.c_int64(), C.c_int()
+    _check(lib().sfft_theorem_params(d, supp, eps, C.byref(r), C.byref(b)))
+    return int(r.value), int(b.value)
+

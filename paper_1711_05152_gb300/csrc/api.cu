@@ -964,6 +964,16 @@ extern "C" int sfft_dimincr_batch(const sfft_params* params, const sfft_sampler*
   });
 }
 
+extern "C" int sfft_theorem_params(int d, int64_t supp, double eps, int64_t* r, int* b) {
+  return guarded([&] {
+    MR1L_REQUIRE(r && b, "null argument");
+    MR1L_REQUIRE(d >= 1 && supp >= 1 && eps > 0.0 && eps < 1.0, "need d >= 1, supp >= 1, 0 < eps < 1");
+    const double lg = std::log(3.0) + std::log((double)d) - std::log(eps);
+    *r = (int64_t)std::ceil(2.0 * (double)supp * (lg + std::log((double)supp)));
+    *b = (int)std::ceil(lg / std::log(2.0));
+  });
+}
+
 extern "C" void sfft_free(sfft_result* res) {
   if (!res) return;
   std::free(res->freqs);

@@ -93,3 +93,16 @@ def test_bspline_sampler_rejects_invalid(lib, groups, orders, msg):
     with pytest.raises(P.Mr1lError) as e:
         P.sfft_dimincr(3, 4, 10, 1, 1e-12, "abs", function=f, stream=0)
     assert e.value.code == P.MR1L_E_INVAL and msg in str(e.value)
+
+
+def test_theorem_params(lib):
+    """The theorem of Section 4: r = ceil(2 supp (ln 3 + ln d + ln supp - ln eps)),
+    b = ceil((ln 3 + ln d - ln eps) / ln 2); d = 5, supp = 1000, eps = 0.01 by hand:
+    ln 3 + ln 5 + ln 1000 - ln 0.01 = ln(1.5e6) = 14.2209..., so r = 28442;
+    ln 3 + ln 5 - ln 0.01 = ln 1500 = 7.3132..., / ln 2 = 10.55, so b = 11."""
+    assert P.theorem_params(5, 1000, 0.01) == (28442, 11)
+    r1, b1 = P.theorem_params(10, 1000, 0.01)
+    r2, b2 = P.theorem_params(10, 1000, 0.001)
+    assert r2 > r1 and b2 >= b1
+    with pytest.raises(P.Mr1lError):
+        P.theorem_params(5, 1000, 1.5)
