@@ -23,6 +23,7 @@
 // Each sub-FFT is a mixed-radix (8, 4, 2, 3) Stockham autosort FFT in shared
 // memory (Govindaraju et al., SC'08 formulation).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -937,15 +938,18 @@ struct TileChoice {
 };
 static std::mutex g_tile_mu;
 static std::map<std::tuple<int, int, int, int>, TileChoice> g_tiles;  // (device, P, mode, df)
-static int g_tune_on = -1;                                            // -1: read MR1L_TILE_TUNE
+static std::atomic<int> g_tune_on{-1};                                // -1: read MR1L_TILE_TUNE
 static int g_forced[2] = {-1, -1};                                    // MR1L_TILES=<col>,<row>
 
 static bool tuning_enabled() {
-  if (g_tune_on < 0) {
+  int on = g_tune_on.load();
+  if (on < 0) {
     const char* e = std::getenv("MR1L_TILE_TUNE");
-    g_tune_on = (e && e[0] == '0') ? 0 : 1;
+    int want = (e && e[0] == '0') ? 0 : 1;
+    g_tune_on.compare_exchange_strong(on, want);  // an explicit mr1l_tune_enable wins
+    on = g_tune_on.load();
   }
-  return g_tune_on != 0;
+  return on != 0;
 }
 
 // Tiles fixed by the environment (MR1L_TILES=<col>,<row>, each one of the
@@ -1057,10 +1061,7 @@ static void launch_first_last(const BlueGeom& g, const BlueIO& io, int ntrans, c
   g_tiles.emplace(key, best);
 }
 
-void tune_enable(int on) {
-  std::lock_guard<std::mutex> lk(g_tile_mu);
-  g_tune_on = on ? 1 : 0;
-}
+void tune_enable(int on) { g_tune_on.store(on ? 1 : 0); }
 
 void tune_reset() {
   std::lock_guard<std::mutex> lk(g_tile_mu);
