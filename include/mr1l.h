@@ -45,13 +45,16 @@
 extern "C" {
 #endif
 
+/* status codes (mr1l_last_error gives the message of the calling thread's
+ * last failure) */
 #define MR1L_OK 0
-#define MR1L_E_INVAL 1
-#define MR1L_E_NOMEM 2
-#define MR1L_E_CUDA 3
-#define MR1L_E_NOT_RECONSTRUCTING 4
-#define MR1L_E_SAMPLER 5
-#define MR1L_E_TIMEOUT 6
+#define MR1L_E_INVAL 1              /* invalid argument or unsupported size */
+#define MR1L_E_NOMEM 2              /* device or host allocation failed */
+#define MR1L_E_CUDA 3               /* a CUDA call or kernel launch failed */
+#define MR1L_E_NOT_RECONSTRUCTING 4 /* MR1L_STRICT: some candidate is in no I_l */
+#define MR1L_E_SAMPLER 5            /* a user sampler callback returned non-zero */
+#define MR1L_E_TIMEOUT 6            /* reserved: no kernel of the library waits on a flag or
+                                       on another CTA, so none can time out */
 
 /* plan flags */
 #define MR1L_STRICT 1           /* fail with E_NOT_RECONSTRUCTING unless condition (2.1) holds */
