@@ -146,6 +146,22 @@ int mr1l_reconstruct(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* 
 int mr1l_evaluate(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode, void* stream);
 
 /*
+ * mr1l_reconstruct_batch / mr1l_evaluate_batch - the transforms of `count`
+ * plans in one call: entry i is mr1l_reconstruct(plans[i], y[i], nrhs[i],
+ * c[i]) (or mr1l_evaluate(plans[i], c[i], nrhs[i], y[i], mode)).  The entries
+ * run on up to 8 internal streams forked from `stream` and joined back into
+ * it, so work queued on `stream` before the call comes first and work queued
+ * after it sees every result.  Entries naming the same plan run in order on
+ * one internal stream (a plan's scratch serves one transform at a time).  The
+ * call fails on the first invalid entry; entries before it may have been
+ * queued.  The paper has no counterpart: it batches independent transforms.
+ */
+int mr1l_reconstruct_batch(mr1l_plan_t* const* plans, int count, const void* const* y, const int* nrhs,
+                           void* const* c, void* stream);
+int mr1l_evaluate_batch(mr1l_plan_t* const* plans, int count, const void* const* c, const int* nrhs,
+                        void* const* y, int mode, void* stream);
+
+/*
  * mr1l_reconstruct_noalloc - the same result as mr1l_reconstruct without any
  * device allocation (the paper has no counterpart; this serves callers that
  * cannot allocate device memory while they run: hosts whose device memory is
@@ -156,7 +172,7 @@ int mr1l_evaluate(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode,
  * the library (32 MiB per GPU that loads it, held until the process exits).
  *   - Fails with MR1L_E_INVAL, naming both numbers, when nrhs * (sum_l M_l +
  *     L * P) exceeds the fixed maximum of 2^21 complex elements (P is the
- *     plan's Bluestein length, the power of two >= 2 max M_l - 1).
+ *     plan's Bluestein length, the smallest 2^k or 3 * 2^k >= 2 max M_l - 1).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

@@ -44,6 +44,7 @@ EXPORTS = [
     "mr1l_plan_masks", "mr1l_destroy", "mr1l_reconstruct", "mr1l_evaluate", "sfft_dimincr",
     "sfft_free", "sfft_dimincr_batch", "mr1l_reconstruct_noalloc", "mr1l_lattice_noise", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
     "mr1l_tune_enable", "mr1l_tune_reset", "mr1l_tune_read", "sfft_theorem_params",
+    "mr1l_reconstruct_batch", "mr1l_evaluate_batch",
 ]
 
 
@@ -143,6 +144,10 @@ def lib() -> C.CDLL:
     L.mr1l_prof_launches.argtypes = []
     L.mr1l_prof_launches.restype = C.c_longlong
     L.mr1l_prof_read.argtypes = [C.c_char_p, C.c_size_t]
+    L.mr1l_reconstruct_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp),
+                                         vp]
+    L.mr1l_evaluate_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp),
+                                      C.c_int, vp]
     L.sfft_theorem_params.argtypes = [C.c_int, C.c_int64, C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_int)]
     L.mr1l_tune_enable.argtypes = [C.c_int]
     L.mr1l_tune_reset.argtypes = []
@@ -480,4 +485,33 @@ def theorem_params(d: int, supp: int, eps: float) -> tuple[int, int]:
     r, b = C.c_int64(), C.c_int()
     _check(lib().sfft_theorem_params(d, supp, eps, C.byref(r), C.byref(b)))
     return int(r.value), int(b.value)
+
+
+def _batch_arrays(plans, xs, width):
+    import torch
+    n = len(plans)
+    hs = (C.c_void_p * max(n, 1))(*[p._h.value for p in plans])
+    ins, outs, nr, keep = (C.c_void_p * max(n, 1))(), (C.c_void_p * max(n, 1))(), (C.c_int * max(n, 1))(), []
+    for i, (p, x) in enumerate(zip(plans, xs)):
+        x2 = x.reshape(-1, width(p, True))
+        if x2.dtype != torch.complex128 or not x2.is_cuda or not x2.is_contiguous():
+            raise TypeError("inputs must be contiguous complex128 CUDA tensors")
+        o = torch.empty((x2.shape[0], width(p, False)), dtype=torch.complex128, device=x2.device)
+        keep += [x2, o]
+        ins[i], outs[i], nr[i] = x2.data_ptr(), o.data_ptr(), x2.shape[0]
+    return hs, ins, outs, nr, keep
+
+
+def reconstruct_batch(plans, ys, stream=None) -> list:
+    """mr1l_reconstruct_batch: Algorithm 2 for each (plan, y) pair in one call."""
+    hs, ins, outs, nr, keep = _batch_arrays(plans, ys, lambda p, inp: p.sum_M if inp else p.nI)
+    _check(lib().mr1l_reconstruct_batch(hs, len(plans), ins, nr, outs, C.c_void_p(_stream(stream))))
+    return keep[1::2]
+
+
+def evaluate_batch(plans, cs, mode: int = MR1L_EVAL, stream=None) -> list:
+    """mr1l_evaluate_batch: lattice evaluation (or the adjoint) for each (plan, c) pair in one call."""
+    hs, ins, outs, nr, keep = _batch_arrays(plans, cs, lambda p, inp: p.nI if inp else p.sum_M)
+    _check(lib().mr1l_evaluate_batch(hs, len(plans), ins, nr, outs, mode, C.c_void_p(_stream(stream))))
+    return keep[1::2]
 

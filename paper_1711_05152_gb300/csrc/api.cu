@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <atomic>
 #include <memory>
 #include <mutex>
@@ -435,53 +436,115 @@ extern "C" int mr1l_plan_masks(const mr1l_plan_t* plan, uint64_t* masks, uint32_
 
 extern "C" void mr1l_destroy(mr1l_plan_t* plan) { delete plan; }
 
+static void reconstruct_impl(mr1l_plan_t* plan, const void* y, int nrhs, void* c, cudaStream_t s) {
+  MR1L_REQUIRE(plan != nullptr, "plan is null");
+  MR1L_REQUIRE(nrhs >= 0 && nrhs <= 65535 / 64, "nrhs out of range");
+  if (nrhs == 0) return;
+  MR1L_REQUIRE(y != nullptr && c != nullptr, "null array");
+  MR1L_REQUIRE(((uintptr_t)y & 15) == 0 && ((uintptr_t)c & 15) == 0, "arrays must be 16-byte aligned");
+  LatticeWork& lw = plan->lw;
+  const int64_t sumM = lw.sumM;
+  plan->C.reserve((size_t)nrhs * sumM);
+  plan->work.reserve((size_t)nrhs * lw.Luse * lw.geom.P);
+  BlueIO io{};
+  io.in = (const cplx*)y;
+  io.in_stride = sumM;
+  io.out = plan->C.get();
+  io.out_stride = sumM;
+  io.work = plan->work.get();
+  blue_run(lw.geom, io, kModeRecon, nrhs, s);
+  gather(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, plan->C.get(), sumM, nrhs, (cplx*)c, plan->nI,
+         nullptr, nullptr, s);
+}
+
+static void evaluate_impl(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode, cudaStream_t s) {
+  MR1L_REQUIRE(plan != nullptr, "plan is null");
+  MR1L_REQUIRE(mode == MR1L_EVAL || mode == MR1L_ADJOINT, "mode must be MR1L_EVAL or MR1L_ADJOINT");
+  MR1L_REQUIRE(nrhs >= 0 && nrhs <= 65535 / 64, "nrhs out of range");
+  if (nrhs == 0) return;
+  MR1L_REQUIRE(y != nullptr && c != nullptr, "null array");
+  MR1L_REQUIRE(((uintptr_t)y & 15) == 0 && ((uintptr_t)c & 15) == 0, "arrays must be 16-byte aligned");
+  LatticeWork& lw = plan->lw;
+  const int64_t sumM = lw.sumM;
+  plan->bins.reserve((size_t)nrhs * sumM);
+  plan->work.reserve((size_t)nrhs * lw.Luse * lw.geom.P);
+  MR1L_CUDA(cudaMemsetAsync(plan->bins.get(), 0, (size_t)nrhs * sumM * sizeof(cplx), s));
+  scatter(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, (const cplx*)c, plan->nI, nrhs,
+          mode == MR1L_ADJOINT, plan->bins.get(), sumM, s);
+  BlueIO io{};
+  io.in = plan->bins.get();
+  io.in_stride = sumM;
+  io.out = (cplx*)y;
+  io.out_stride = sumM;
+  io.work = plan->work.get();
+  blue_run(lw.geom, io, kModeEval, nrhs, s);
+}
+
 extern "C" int mr1l_reconstruct(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* stream) {
-  return guarded([&] {
-    MR1L_REQUIRE(plan != nullptr, "plan is null");
-    MR1L_REQUIRE(nrhs >= 0 && nrhs <= 65535 / 64, "nrhs out of range");
-    if (nrhs == 0) return;
-    MR1L_REQUIRE(y != nullptr && c != nullptr, "null array");
-    MR1L_REQUIRE(((uintptr_t)y & 15) == 0 && ((uintptr_t)c & 15) == 0, "arrays must be 16-byte aligned");
-    cudaStream_t s = (cudaStream_t)stream;
-    LatticeWork& lw = plan->lw;
-    const int64_t sumM = lw.sumM;
-    plan->C.reserve((size_t)nrhs * sumM);
-    plan->work.reserve((size_t)nrhs * lw.Luse * lw.geom.P);
-    BlueIO io{};
-    io.in = (const cplx*)y;
-    io.in_stride = sumM;
-    io.out = plan->C.get();
-    io.out_stride = sumM;
-    io.work = plan->work.get();
-    blue_run(lw.geom, io, kModeRecon, nrhs, s);
-    gather(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, plan->C.get(), sumM, nrhs, (cplx*)c, plan->nI,
-           nullptr, nullptr, s);
-  });
+  return guarded([&] { reconstruct_impl(plan, y, nrhs, c, (cudaStream_t)stream); });
 }
 
 extern "C" int mr1l_evaluate(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode, void* stream) {
+  return guarded([&] { evaluate_impl(plan, c, nrhs, y, mode, (cudaStream_t)stream); });
+}
+
+// Runs body(i, stream_i) for i < count on up to kBatchStreams streams forked
+// from s (they wait for the work already queued on s) and joined back into s.
+// Entries with the same plan share a stream, since a plan's scratch buffers
+// serve one transform at a time.
+constexpr int kBatchStreams = 8;
+template <class F>
+static void fork_join(mr1l_plan_t* const* plans, int count, cudaStream_t s, F&& body) {
+  if (count <= 0) return;
+  const int ns = std::min(count, kBatchStreams);
+  struct Res {
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ev;
+    ~Res() {
+      for (auto e : ev)
+        if (e) cudaEventDestroy(e);
+      for (auto x : st)
+        if (x) cudaStreamDestroy(x);
+    }
+  } r;
+  r.st.assign(ns, nullptr);
+  r.ev.assign(ns + 1, nullptr);
+  for (auto& e : r.ev) MR1L_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  for (auto& x : r.st) MR1L_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  MR1L_CUDA(cudaEventRecord(r.ev[ns], s));
+  for (auto x : r.st) MR1L_CUDA(cudaStreamWaitEvent(x, r.ev[ns], 0));
+  std::map<const mr1l_plan_t*, int> lane;
+  int next = 0;
+  for (int i = 0; i < count; ++i) {
+    auto it = lane.find(plans[i]);
+    const int k = it != lane.end() ? it->second : (lane[plans[i]] = next++ % ns);
+    body(i, r.st[k]);
+  }
+  for (int k = 0; k < ns; ++k) {
+    MR1L_CUDA(cudaEventRecord(r.ev[k], r.st[k]));
+    MR1L_CUDA(cudaStreamWaitEvent(s, r.ev[k], 0));
+  }
+}
+
+extern "C" int mr1l_reconstruct_batch(mr1l_plan_t* const* plans, int count, const void* const* y, const int* nrhs,
+                                      void* const* c, void* stream) {
   return guarded([&] {
-    MR1L_REQUIRE(plan != nullptr, "plan is null");
-    MR1L_REQUIRE(mode == MR1L_EVAL || mode == MR1L_ADJOINT, "mode must be MR1L_EVAL or MR1L_ADJOINT");
-    MR1L_REQUIRE(nrhs >= 0 && nrhs <= 65535 / 64, "nrhs out of range");
-    if (nrhs == 0) return;
-    MR1L_REQUIRE(y != nullptr && c != nullptr, "null array");
-    MR1L_REQUIRE(((uintptr_t)y & 15) == 0 && ((uintptr_t)c & 15) == 0, "arrays must be 16-byte aligned");
-    cudaStream_t s = (cudaStream_t)stream;
-    LatticeWork& lw = plan->lw;
-    const int64_t sumM = lw.sumM;
-    plan->bins.reserve((size_t)nrhs * sumM);
-    plan->work.reserve((size_t)nrhs * lw.Luse * lw.geom.P);
-    MR1L_CUDA(cudaMemsetAsync(plan->bins.get(), 0, (size_t)nrhs * sumM * sizeof(cplx), s));
-    scatter(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, (const cplx*)c, plan->nI, nrhs,
-            mode == MR1L_ADJOINT, plan->bins.get(), sumM, s);
-    BlueIO io{};
-    io.in = plan->bins.get();
-    io.in_stride = sumM;
-    io.out = (cplx*)y;
-    io.out_stride = sumM;
-    io.work = plan->work.get();
-    blue_run(lw.geom, io, kModeEval, nrhs, s);
+    MR1L_REQUIRE(count >= 0, "count must be >= 0");
+    if (count == 0) return;
+    MR1L_REQUIRE(plans && y && nrhs && c, "null argument");
+    fork_join(plans, count, (cudaStream_t)stream,
+              [&](int i, cudaStream_t si) { reconstruct_impl(plans[i], y[i], nrhs[i], c[i], si); });
+  });
+}
+
+extern "C" int mr1l_evaluate_batch(mr1l_plan_t* const* plans, int count, const void* const* c, const int* nrhs,
+                                   void* const* y, int mode, void* stream) {
+  return guarded([&] {
+    MR1L_REQUIRE(count >= 0, "count must be >= 0");
+    if (count == 0) return;
+    MR1L_REQUIRE(plans && c && nrhs && y, "null argument");
+    fork_join(plans, count, (cudaStream_t)stream,
+              [&](int i, cudaStream_t si) { evaluate_impl(plans[i], c[i], nrhs[i], y[i], mode, si); });
   });
 }
 

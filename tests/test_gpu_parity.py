@@ -290,3 +290,25 @@ def test_sfft_d2_and_caps():
     ref = sfft.sfft(sig, 25, 25, 2, 10, 1e-12, "rel", seed=8)
     _assert_sfft_equal(out, ref)
     assert out.freqs.shape[0] == 25
+
+
+def test_batched_plans_match_single_calls():
+    """mr1l_reconstruct_batch / mr1l_evaluate_batch over plans of different
+    sizes (one listed twice) give exactly the single-call results."""
+    rng = np.random.default_rng(77)
+    plans, ys, cs = [], [], []
+    for n, t, N in [(50, 2, 5), (1500, 4, 8), (9000, 5, 9)]:
+        J = _rand_set(rng, n, t, N)
+        pl = P.plan_search(J, seed=n)
+        plans.append(pl)
+        ys.append(torch.from_numpy(rng.standard_normal((2, pl.sum_M)) + 1j * rng.standard_normal((2, pl.sum_M))).cuda())
+        cs.append(torch.from_numpy(rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))).cuda())
+    plans.append(plans[1])
+    ys.append(ys[1] * 2)
+    cs.append(cs[1] * 2)
+    got = P.reconstruct_batch(plans, ys)
+    gote = P.evaluate_batch(plans, cs, P.MR1L_ADJOINT)
+    torch.cuda.synchronize()
+    for pl, y, c, g, ge in zip(plans, ys, cs, got, gote):
+        np.testing.assert_array_equal(g.cpu().numpy(), pl.reconstruct(y).cpu().numpy())
+        np.testing.assert_array_equal(ge.cpu().numpy(), pl.evaluate(c, P.MR1L_ADJOINT).cpu().numpy())
