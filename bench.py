@@ -237,6 +237,53 @@ def oracle_sample(name: str, wl, outs) -> dict:
                       f"thread), time scaled by samples"}
 
 
+def _oracle_job(job):
+    """One worker of the all-cores leg: the bounded oracle sample on one
+    signal of the workload (its own seed).  Returns (samples, start, end) on
+    the host's wall clock."""
+    name, seed, t_stop = job
+    from oracle import sfft as osfft
+    sig, p = W.workload(name, seed)
+    t0 = time.time()
+    res = osfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=seed,
+                     t_stop=t_stop)
+    return res.samples, t0, time.time()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_all_cores(name: str, wl, outs, cores: int | None = None, t_stop: int | None = None) -> dict:
+    """The same bounded oracle sample on every host core at once: one
+    single-threaded process per core (spawned, so no process inherits a CUDA
+    context), each on its own signal of the workload, seeds seed, seed + 1, ...
+    Throughput = all samples / the wall time from the first start to the last
+    end, scaled to detected coefficients by the timed job's coefficients per
+    sample."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    cores = cores or host_cores()
+    if t_stop is None:
+        t_stop = 6 if name == "plain_d10" else 3
+    full_samples = sum(o.samples for o in outs)
+    full_detected = sum(o.freqs.shape[0] for o in outs)
+    jobs = [(name, wl.seeds[0] + i, t_stop) for i in range(cores)]
+    # a worker that dies raises BrokenProcessPool here instead of hanging
+    with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
+        res = list(pool.map(_oracle_job, jobs))
+    samples = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    value = samples / wall * full_detected / max(full_samples, 1)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle increments t<={t_stop} of {name} seeds {jobs[0][1]}..{jobs[-1][1]}, one "
+                      f"single-threaded process per core: {samples} samples in {wall:.1f} s wall, "
+                      f"scaled by the timed job's coefficients per sample"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -428,9 +475,11 @@ def run_ours(args):
     kernel_share = {k: round(v["ms"] / total_prof_ms, 4) for k, v in
                     sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]}
 
-    cpu = None
+    cpu = cpu_all = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(args.workload, wl, last)
+        if args.workload != "batch256":
+            cpu_all = oracle_sample_all_cores(args.workload, wl, last)
 
     form_b, form_p = FORMS[args.workload]
     line = {
@@ -463,6 +512,7 @@ def run_ours(args):
         "tile_tuner": tile_summary(P.tune_read()),
         "clocks": clock_info,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "detected": int(sum(o.freqs.shape[0] for o in last)), "support_exact": wl.exact(last),
         "samples": int(sum(o.samples for o in last)),
     }

@@ -3,6 +3,7 @@ for Table 5.7 against the oracle's evaluator, and the paper fixtures it reads.""
 
 import importlib.util
 import os
+import sys
 
 import numpy as np
 
@@ -14,8 +15,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _bench():
-    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    # registered under its own name, so that spawned workers can import it
+    if "bench" in sys.modules:
+        return sys.modules["bench"]
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
     mod = importlib.util.module_from_spec(spec)
+    sys.modules["bench"] = mod
     spec.loader.exec_module(mod)
     return mod
 
@@ -39,3 +44,17 @@ def test_paper_fixtures_parse():
     assert len(bench._paper_rows("paper_table_5_4.txt")) == 18
     t57 = bench._paper_rows("paper_table_5_7.txt")
     assert len(t57) == 13 and t57[-1][:3] == [64.0, 10000.0, 2639274025.0]
+
+
+def test_all_cores_oracle_leg_runs():
+    """The all-cores CPU leg (spawned single-threaded oracle processes, one
+    signal each) on the d = 3 workload with two processes: every process
+    finishes, and the rate is scaled by the timed job's coefficients per
+    sample."""
+    bench = _bench()
+    sig, p = W.workload("tiny_d3", 1)
+    ref = sfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=1)
+    wl = type("WL", (), {"seeds": [1]})()
+    out = bench.oracle_sample_all_cores("tiny_d3", wl, [ref], cores=2, t_stop=3)
+    assert out["cores"] == 2 and out["kind"] == "oracle" and out["value"] > 0
+    assert "seeds 1..2" in out["sample"]
