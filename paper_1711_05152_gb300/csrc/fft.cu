@@ -148,6 +148,132 @@ __device__ __forceinline__ void reg_dft8_half(typename O::V* v) {
 }
 
 // ---------------------------------------------------------------------------
+// Twiddled radix-8, -4 and -2 butterflies in multiply-add form (FP64), after
+// Goedecker, "Fast radix 2, 3, 4, and 5 kernels for fast Fourier
+// transformations on computers with overlapping multiply-add instructions",
+// SIAM J. Sci. Comput. 18 (1997).  A twiddle w = s (1 + i t) is held as the
+// pair (s, t); then the two outputs x +- w y cost two FMAs for u = (1 + i t) y
+// and four for x +- s u, against four for the product and four for the sums.
+// The butterfly on inputs v_r w^r (w = exp(-+2 pi i k / (R Ns))) is split into
+// radix-2 levels that factor the twiddles out, so that each of its radix-2
+// steps has that form:
+//   radix 8: level 1 pairs (v_r, v_r+4) under w^4; level 2 under w^2 and
+//            -+i w^2; level 3 under w, w8 w, -+i w, -+i w8 w
+//            (w8 = exp(-+2 pi i / 8)): 72 FMAs against 80 instructions
+//            (28 for the seven products, 52 for the DFT);
+//   radix 4: w^2, then w and -+i w: 24 against 28;  radix 2: 6 against 8.
+// Multiplying by -+i is a swap of components.  The first-level twiddle (angle
+// pi k / Ns) reaches pi / 2 at k = Ns / 2; from there on the table holds
+// +-i times it (cosine > 0 again) and the butterfly turns u back by -+i.
+// ---------------------------------------------------------------------------
+// (1 + i t) y
+__device__ __forceinline__ cplx fma_rot(cplx y, double t) { return cmake(fma(-t, y.y, y.x), fma(t, y.x, y.y)); }
+// p = x + s u, m = x - s u
+__device__ __forceinline__ void fma_bfly(cplx x, double s, cplx u, cplx& p, cplx& m) {
+  p = cmake(fma(s, u.x, x.x), fma(s, u.y, x.y));
+  m = cmake(fma(-s, u.x, x.x), fma(-s, u.y, x.y));
+}
+
+template <int R, bool INV>
+struct FmaDft;
+
+template <bool INV>
+struct FmaDft<8, INV> {
+  // e = (s, t) of w^4 (turned when half), w^2, w, w8 w
+  static __device__ __forceinline__ void run(cplx* v, const cplx* e, bool half) {
+    const cplx T4 = e[0], T2 = e[1], T1 = e[2], TW = e[3];
+    const double t4 = INV ? -T4.y : T4.y, t2 = INV ? -T2.y : T2.y;
+    const double t1 = INV ? -T1.y : T1.y, tw = INV ? -TW.y : TW.y;
+    cplx a[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // (v_q, v_q+4) under w^4
+      cplx u = fma_rot(v[q + 4], t4);
+      const cplx ut = mul_mi<INV>(u);
+      u = half ? ut : u;
+      fma_bfly(v[q], T4.x, u, a[q], a[q + 4]);
+    }
+    // even half (a0, a2 | a4, a6), odd half (a1, a3 | a5, a7)
+    cplx E0, E1, E2, E3, o0, o1, o2, o3;
+    fma_bfly(a[0], T2.x, fma_rot(a[2], t2), E0, E2);
+    fma_bfly(a[4], T2.x, mul_mi<INV>(fma_rot(a[6], t2)), E1, E3);
+    fma_bfly(a[1], T2.x, fma_rot(a[3], t2), o0, o2);
+    fma_bfly(a[5], T2.x, mul_mi<INV>(fma_rot(a[7], t2)), o1, o3);
+    fma_bfly(E0, T1.x, fma_rot(o0, t1), v[0], v[4]);
+    fma_bfly(E1, TW.x, fma_rot(o1, tw), v[1], v[5]);
+    fma_bfly(E2, T1.x, mul_mi<INV>(fma_rot(o2, t1)), v[2], v[6]);
+    fma_bfly(E3, TW.x, mul_mi<INV>(fma_rot(o3, tw)), v[3], v[7]);
+  }
+};
+
+template <bool INV>
+struct FmaDft<4, INV> {
+  // e = (s, t) of w^2 (turned when half), w
+  static __device__ __forceinline__ void run(cplx* v, const cplx* e, bool half) {
+    const cplx T2 = e[0], T1 = e[1];
+    const double t2 = INV ? -T2.y : T2.y, t1 = INV ? -T1.y : T1.y;
+    cplx A0, A1, B0, B1;
+    cplx u = fma_rot(v[2], t2), ut = mul_mi<INV>(u);
+    fma_bfly(v[0], T2.x, half ? ut : u, A0, A1);
+    u = fma_rot(v[3], t2);
+    ut = mul_mi<INV>(u);
+    fma_bfly(v[1], T2.x, half ? ut : u, B0, B1);
+    fma_bfly(A0, T1.x, fma_rot(B0, t1), v[0], v[2]);
+    fma_bfly(A1, T1.x, mul_mi<INV>(fma_rot(B1, t1)), v[1], v[3]);
+  }
+};
+
+template <bool INV>
+struct FmaDft<2, INV> {
+  // e = (s, t) of w (turned when half)
+  static __device__ __forceinline__ void run(cplx* v, const cplx* e, bool half) {
+    const cplx T = e[0];
+    cplx u = fma_rot(v[1], INV ? -T.y : T.y);
+    const cplx ut = mul_mi<INV>(u);
+    fma_bfly(v[0], T.x, half ? ut : u, v[0], v[1]);
+  }
+};
+
+template <class O, int R>
+struct FmaForm {
+  static constexpr bool value = std::is_same<O, OpsF64>::value && (R == 2 || R == 4 || R == 8);
+};
+template <class O>
+struct FmaTab {  // the multiply-add twiddles: FP64 only
+  static __device__ __forceinline__ const cplx* of(const typename O::V*) { return nullptr; }
+};
+template <>
+struct FmaTab<OpsF64> {
+  static __device__ __forceinline__ const cplx* of(const cplx* twn) { return twn + kSmallTw; }
+};
+template <int R>
+__device__ __forceinline__ int fma_off(int Ns, int k) {
+  return R == 8 ? 4 * (Ns - 1 + k) : R == 4 ? 4 * kFmaSpan + 2 * (Ns - 1 + k) : 6 * kFmaSpan + (Ns - 1 + k);
+}
+
+// The DFT of one radix-R butterfly of a stage with stride Ns, including the
+// stage twiddles w^r (w = exp(-+2 pi i k / (R Ns)), none when Ns = 1).
+template <int R, bool INV, class O>
+__device__ __forceinline__ void twiddled_dft(typename O::V* v, int n, int Ns, int k, const typename O::V* twn_n,
+                                             const cplx* ft) {
+  if constexpr (FmaForm<O, R>::value) {
+    if (Ns > 1) {
+      FmaDft<R, INV>::run(v, ft + fma_off<R>(Ns, k), 2 * k >= Ns);
+      return;
+    }
+  } else {
+    if (Ns > 1) {
+      const int step = k * (n / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const typename O::V w = twn_n[r * step];
+        v[r] = INV ? O::mulc(v[r], w) : O::mul(v[r], w);
+      }
+    }
+  }
+  RegDft<R, INV, O>::run(v);
+}
+
+// ---------------------------------------------------------------------------
 // One Stockham stage of radix R over nseq sequences of length n in shared
 // memory; element i of sequence b sits at s[b * bs + i * is].  The block has
 // nseq * n / 8 threads (or more, which idle); each thread runs up to
@@ -158,7 +284,7 @@ __device__ __forceinline__ void reg_dft8_half(typename O::V* v) {
 // ---------------------------------------------------------------------------
 template <int R, bool INV, bool COLS, class O, bool HALF = false>
 __device__ __forceinline__ void stockham_stage(typename O::V* s, int n, int Ns, int nseq, int bs, int is,
-                                               const typename O::V* twn_n) {
+                                               const typename O::V* twn_n, const cplx* ft) {
   typedef typename O::V V;
   constexpr int CNT = (8 + R - 1) / R;
   const int nb = n / R;
@@ -189,15 +315,7 @@ __device__ __forceinline__ void stockham_stage(typename O::V* s, int n, int Ns, 
       const V* src = s + b * bs + j * is;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[c][r] = src[r * nb * is];
-      if (Ns > 1) {
-        int step = k * (n / (Ns * R));
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          V w = twn_n[r * step];
-          v[c][r] = INV ? O::mulc(v[c][r], w) : O::mul(v[c][r], w);
-        }
-      }
-      RegDft<R, INV, O>::run(v[c]);
+      twiddled_dft<R, INV, O>(v[c], n, Ns, k, twn_n, ft);
     }
   }
   __syncthreads();
@@ -225,28 +343,29 @@ template <bool INV, bool COLS, class O, bool HALF_FIRST = false>
 __device__ __forceinline__ void smem_fft(typename O::V* s, int n, int nseq, int bs, int is,
                                          const typename O::V* twn) {
   const typename O::V* twn_n = twiddles_of(twn, n);
+  const cplx* ft = FmaTab<O>::of(twn);
   const bool three = (n % 3) == 0;
   int rem = 31 - __clz(three ? n / 3 : n);  // log2 of the power-of-two part
   int Ns = 1;
   if (HALF_FIRST && rem >= 3) {
-    stockham_stage<8, INV, COLS, O, true>(s, n, Ns, nseq, bs, is, twn_n);
+    stockham_stage<8, INV, COLS, O, true>(s, n, Ns, nseq, bs, is, twn_n, ft);
     Ns <<= 3;
     rem -= 3;
   }
   while (rem >= 3) {
-    stockham_stage<8, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n);
+    stockham_stage<8, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n, ft);
     Ns <<= 3;
     rem -= 3;
   }
   if (rem == 2) {
-    stockham_stage<4, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n);
+    stockham_stage<4, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n, ft);
     Ns <<= 2;
   }
   if (rem == 1) {
-    stockham_stage<2, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n);
+    stockham_stage<2, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n, ft);
     Ns <<= 1;
   }
-  if (three) stockham_stage<3, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n);
+  if (three) stockham_stage<3, INV, COLS, O>(s, n, Ns, nseq, bs, is, twn_n, ft);
 }
 
 // ---------------------------------------------------------------------------
@@ -520,8 +639,8 @@ struct RowStoreScaled {  // filter spectrum <- v / P
 // One radix-R Stockham stage over nrows rows of length n, element-fastest;
 // element i of row b is read as src.ld(b, i) and written as dst.st(b, i, v).
 template <int R, bool INV, class O, class Src, class Dst>
-__device__ __forceinline__ void row_stage(int n, int Ns, int nrows, const typename O::V* twn_n, const Src& src,
-                                          const Dst& dst) {
+__device__ __forceinline__ void row_stage(int n, int Ns, int nrows, const typename O::V* twn_n, const cplx* ft,
+                                          const Src& src, const Dst& dst) {
   typedef typename O::V V;
   constexpr int CNT = (8 + R - 1) / R;
   const int nb = n / R;
@@ -539,15 +658,7 @@ __device__ __forceinline__ void row_stage(int n, int Ns, int nrows, const typena
     if (act[c]) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[c][r] = src.ld(b, j + r * nb);
-      if (Ns > 1) {
-        const int step = k * (n / (Ns * R));
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const V w = twn_n[r * step];
-          v[c][r] = INV ? O::mulc(v[c][r], w) : O::mul(v[c][r], w);
-        }
-      }
-      RegDft<R, INV, O>::run(v[c]);
+      twiddled_dft<R, INV, O>(v[c], n, Ns, k, twn_n, ft);
     }
   }
   __syncthreads();
@@ -568,21 +679,22 @@ template <bool INV, class O, class Src, class Dst>
 __device__ __forceinline__ void row_fft_io(typename O::V* sm, int P2, int nrows, const typename O::V* twn,
                                            const Src& src, const Dst& dst) {
   const typename O::V* tw = twiddles_of(twn, P2);
+  const cplx* ft = FmaTab<O>::of(twn);
   const RowSmem<O> smio{sm, P2};
   const int b = 31 - __clz(P2), n8 = b / 3, tail = b % 3;
-  row_stage<8, INV, O>(P2, 1, nrows, tw, src, smio);
+  row_stage<8, INV, O>(P2, 1, nrows, tw, ft, src, smio);
   int Ns = 8;
   const int mid = n8 - 1 - (tail == 0 ? 1 : 0);
   for (int i = 0; i < mid; ++i) {
-    row_stage<8, INV, O>(P2, Ns, nrows, tw, smio, smio);
+    row_stage<8, INV, O>(P2, Ns, nrows, tw, ft, smio, smio);
     Ns <<= 3;
   }
   if (tail == 0)
-    row_stage<8, INV, O>(P2, Ns, nrows, tw, smio, dst);
+    row_stage<8, INV, O>(P2, Ns, nrows, tw, ft, smio, dst);
   else if (tail == 2)
-    row_stage<4, INV, O>(P2, Ns, nrows, tw, smio, dst);
+    row_stage<4, INV, O>(P2, Ns, nrows, tw, ft, smio, dst);
   else
-    row_stage<2, INV, O>(P2, Ns, nrows, tw, smio, dst);
+    row_stage<2, INV, O>(P2, Ns, nrows, tw, ft, smio, dst);
 }
 
 // Pass 2: rows.  FILTER: forward FFT scaled by 1/P into Bh.  Otherwise forward
@@ -666,6 +778,42 @@ __global__ void small_twiddle_kernel(cplx* tw) {
   tw[i] = cmake(cs, -sn);
 }
 
+// The multiply-add twiddles (s, t), w = s (1 + i t), of the stage stride Ns
+// and butterfly k < Ns; angles are exact multiples of pi / (4 Ns):
+//   radix 8: w^4 (pi k / Ns, turned past pi / 2), w^2, w, w8 w
+//   radix 4: w^2 (pi k / Ns, turned), w;     radix 2: w (pi k / Ns, turned)
+// (w = exp(-2 pi i k / (R Ns))).  "Turned" entries, 2 k >= Ns, hold i w = s
+// (1 + i t) with s = sin, t = cos / sin of the angle; the others s = cos,
+// t = -tan (cosine > 0 in both).
+__global__ void fma_twiddle_kernel(cplx* ft) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kFmaTw) return;
+  int per, rel, R;
+  if (i < 4 * kFmaSpan) {
+    R = 8, per = 4, rel = i;
+  } else if (i < 6 * kFmaSpan) {
+    R = 4, per = 2, rel = i - 4 * kFmaSpan;
+  } else {
+    R = 2, per = 1, rel = i - 6 * kFmaSpan;
+  }
+  const int idx = rel / per, which = rel - idx * per;  // idx = Ns - 1 + k
+  const int Ns = 1 << (31 - __clz(idx + 1)), k = idx + 1 - Ns;
+  // angle / pi of the entry (forward sign taken below)
+  double f;
+  bool turned = false;
+  if (which == 0) {
+    f = (double)k / (double)Ns;  // w^4, w^2 or w of radix 8, 4, 2: pi k / Ns
+    turned = 2 * k >= Ns;
+  } else if (R == 8) {
+    f = which == 1 ? (double)k / (2.0 * Ns) : which == 2 ? (double)k / (4.0 * Ns) : (double)(k + Ns) / (4.0 * Ns);
+  } else {
+    f = (double)k / (2.0 * Ns);  // radix 4: w
+  }
+  double sn, cs;
+  sincospi(f, &sn, &cs);  // w = cs - i sn
+  ft[i] = turned ? cmake(sn, cs / sn) : cmake(cs, -sn / cs);
+}
+
 // Chirp w[n] = exp(-pi i q / M), q = n^2 mod 2M (exact), as the product of two
 // tabulated factors exp(-pi i (q >> 12) 4096 / M) * exp(-pi i (q & 4095) / M):
 // per-lattice tables of kChirpLo and kChirpSeedLen - kChirpLo entries (2M <=
@@ -735,10 +883,12 @@ const cplx* small_twiddles(cudaStream_t s) {
   auto it = g_twn.find(dev);
   if (it != g_twn.end()) return it->second;
   cplx* p = nullptr;
-  MR1L_CUDA(cudaMalloc(&p, kSmallTw * sizeof(cplx)));
+  MR1L_CUDA(cudaMalloc(&p, (kSmallTw + kFmaTw) * sizeof(cplx)));
   MR1L_CUDA(cudaMemsetAsync(p, 0, kSmallTw * sizeof(cplx), s));
   MR1L_LAUNCH("small_twiddle_kernel", s, 0, 16.0 * kSmallTw,
               small_twiddle_kernel<<<cdiv(kSmallTw, 256), 256, 0, s>>>(p));
+  MR1L_LAUNCH("fma_twiddle_kernel", s, 0, 16.0 * kFmaTw,
+              fma_twiddle_kernel<<<cdiv(kFmaTw, 256), 256, 0, s>>>(p + kSmallTw));
   MR1L_CUDA(cudaStreamSynchronize(s));
   g_twn[dev] = p;
   return p;

@@ -27,8 +27,9 @@ struct BlueGeom {
   const cplx* ws;       // device [sum M]: chirp / M
   cplx* Bh;             // device [L][P]: filter spectrum FFT_P(b) / P (pass order)
   const cplx* tw;       // device [P]: exp(-2 pi i e / P)
-  const cplx* twn;      // device [kSmallTw]: exp(-2 pi i e / n), n = 2^a <= 8192 at offset n,
-                        //   n = 3 * 2^a <= 6144 at offset kSmallTwPow2 + n - 3
+  const cplx* twn;      // device [kSmallTw + kFmaTw]: exp(-2 pi i e / n), n = 2^a <= 8192 at offset n,
+                        //   n = 3 * 2^a <= 6144 at offset kSmallTwPow2 + n - 3; then the
+                        //   multiply-add twiddles (kFmaTw)
   int64_t sum_M;        // host: sum of the L lattice sizes (for launch accounting)
   // double-float arithmetic (df != 0): the same tables as hi/lo FP32 pairs
   // (float4 = re.hi, re.lo, im.hi, im.lo); Bh then holds float4 data
@@ -63,6 +64,14 @@ struct BlueIO {
 constexpr int kSmallMax = 4096;  // P <= 4096: one CTA holds the whole transform
 constexpr int kSmallTwPow2 = 16384;  // power-of-two sub-FFT lengths up to 8192
 constexpr int kSmallTw = kSmallTwPow2 + 12288;
+// Twiddles of the FP64 multiply-add butterflies, stored after the kSmallTw
+// small twiddles in the same allocation as (s, t) pairs (w = s (1 + i t)):
+// for radix 8, 4 and 2 and every stage stride Ns = 2^e <= kFmaMaxNs, the
+// entries of k < Ns sit at index Ns - 1 + k of the radix's region, 4, 2 and 1
+// pairs per index.
+constexpr int kFmaMaxNs = 4096;
+constexpr int kFmaSpan = 2 * kFmaMaxNs - 1;
+constexpr int kFmaTw = 7 * kFmaSpan;
 
 // Device-resident twiddle tables, cached per (device, P).
 const cplx* twiddle_table(int P, cudaStream_t s);
