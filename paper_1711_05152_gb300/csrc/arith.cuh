@@ -27,6 +27,10 @@ struct OpsF64 {
   static __device__ __forceinline__ V sub(V a, V b) { return csub(a, b); }
   static __device__ __forceinline__ V mul(V a, V b) { return cmul(a, b); }
   static __device__ __forceinline__ V mulc(V a, V b) { return cmulc(a, b); }
+  // acc + a * b as four FMAs
+  static __device__ __forceinline__ V mac(V acc, V a, V b) {
+    return cmake(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+  }
   static __device__ __forceinline__ V conj(V a) { return cconj(a); }
   template <bool INV>
   static __device__ __forceinline__ V mi(V a) { return mul_mi<INV>(a); }
@@ -126,6 +130,7 @@ struct OpsDF {
     dw_dot2(a.x, a.y, b.z, b.w, a.z, a.w, b.x, b.y, 1.f, r.z, r.w);   // ar bi + ai br
     return r;
   }
+  static __device__ __forceinline__ V mac(V acc, V a, V b) { return add(acc, mul(a, b)); }
   // a * conj(b)
   static __device__ __forceinline__ V mulc(V a, V b) {
     V r;

@@ -163,8 +163,10 @@ __device__ __forceinline__ void reg_dft8_half(typename O::V* v) {
 //            (28 for the seven products, 52 for the DFT);
 //   radix 4: w^2, then w and -+i w: 24 against 28;  radix 2: 6 against 8.
 // Multiplying by -+i is a swap of components.  The first-level twiddle (angle
-// pi k / Ns) reaches pi / 2 at k = Ns / 2; from there on the table holds
-// +-i times it (cosine > 0 again) and the butterfly turns u back by -+i.
+// pi k / Ns) reaches pi / 2 at k = Ns / 2; from there on ("turned") the
+// butterfly swaps the components of y and of one output pair instead, with
+// the table's (s, t) taken for i w (fma_bfly_turnable), so that no negated
+// value has to be materialised.
 // ---------------------------------------------------------------------------
 // (1 + i t) y
 __device__ __forceinline__ cplx fma_rot(cplx y, double t) { return cmake(fma(-t, y.y, y.x), fma(t, y.x, y.y)); }
@@ -172,6 +174,27 @@ __device__ __forceinline__ cplx fma_rot(cplx y, double t) { return cmake(fma(-t,
 __device__ __forceinline__ void fma_bfly(cplx x, double s, cplx u, cplx& p, cplx& m) {
   p = cmake(fma(s, u.x, x.x), fma(s, u.y, x.y));
   m = cmake(fma(-s, u.x, x.x), fma(-s, u.y, x.y));
+}
+
+// p, m = x +- w y for the first-level twiddle w = (s, t).  Not turned:
+// w = s (1 + i t).  Turned (forward): i w = s (1 - i t), i.e. w y = s ((a -
+// t b) - i (b + t a)) with (a, b) = (Im y, Re y); the inverse takes the
+// conjugate (t -> -t, the sign on the real part instead).  The swaps are
+// register selects.
+template <bool INV>
+__device__ __forceinline__ void fma_bfly_turnable(cplx x, cplx T, cplx y, bool turned, cplx& p, cplx& m) {
+  const double t = INV ? -T.y : T.y;
+  const double a = turned ? y.y : y.x, b = turned ? y.x : y.y;
+  const double ux = fma(-t, b, a), uy = fma(t, a, b);
+  const double px = fma(T.x, ux, x.x), mx = fma(-T.x, ux, x.x);
+  const double py = fma(T.x, uy, x.y), my = fma(-T.x, uy, x.y);
+  if (INV) {
+    p = cmake(turned ? mx : px, py);
+    m = cmake(turned ? px : mx, my);
+  } else {
+    p = cmake(px, turned ? my : py);
+    m = cmake(mx, turned ? py : my);
+  }
 }
 
 template <int R, bool INV>
@@ -182,16 +205,10 @@ struct FmaDft<8, INV> {
   // e = (s, t) of w^4 (turned when half), w^2, w, w8 w
   static __device__ __forceinline__ void run(cplx* v, const cplx* e, bool half) {
     const cplx T4 = e[0], T2 = e[1], T1 = e[2], TW = e[3];
-    const double t4 = INV ? -T4.y : T4.y, t2 = INV ? -T2.y : T2.y;
-    const double t1 = INV ? -T1.y : T1.y, tw = INV ? -TW.y : TW.y;
+    const double t2 = INV ? -T2.y : T2.y, t1 = INV ? -T1.y : T1.y, tw = INV ? -TW.y : TW.y;
     cplx a[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {  // (v_q, v_q+4) under w^4
-      cplx u = fma_rot(v[q + 4], t4);
-      const cplx ut = mul_mi<INV>(u);
-      u = half ? ut : u;
-      fma_bfly(v[q], T4.x, u, a[q], a[q + 4]);
-    }
+    for (int q = 0; q < 4; ++q) fma_bfly_turnable<INV>(v[q], T4, v[q + 4], half, a[q], a[q + 4]);  // under w^4
     // even half (a0, a2 | a4, a6), odd half (a1, a3 | a5, a7)
     cplx E0, E1, E2, E3, o0, o1, o2, o3;
     fma_bfly(a[0], T2.x, fma_rot(a[2], t2), E0, E2);
@@ -210,13 +227,10 @@ struct FmaDft<4, INV> {
   // e = (s, t) of w^2 (turned when half), w
   static __device__ __forceinline__ void run(cplx* v, const cplx* e, bool half) {
     const cplx T2 = e[0], T1 = e[1];
-    const double t2 = INV ? -T2.y : T2.y, t1 = INV ? -T1.y : T1.y;
+    const double t1 = INV ? -T1.y : T1.y;
     cplx A0, A1, B0, B1;
-    cplx u = fma_rot(v[2], t2), ut = mul_mi<INV>(u);
-    fma_bfly(v[0], T2.x, half ? ut : u, A0, A1);
-    u = fma_rot(v[3], t2);
-    ut = mul_mi<INV>(u);
-    fma_bfly(v[1], T2.x, half ? ut : u, B0, B1);
+    fma_bfly_turnable<INV>(v[0], T2, v[2], half, A0, A1);
+    fma_bfly_turnable<INV>(v[1], T2, v[3], half, B0, B1);
     fma_bfly(A0, T1.x, fma_rot(B0, t1), v[0], v[2]);
     fma_bfly(A1, T1.x, mul_mi<INV>(fma_rot(B1, t1)), v[1], v[3]);
   }
@@ -226,10 +240,10 @@ template <bool INV>
 struct FmaDft<2, INV> {
   // e = (s, t) of w (turned when half)
   static __device__ __forceinline__ void run(cplx* v, const cplx* e, bool half) {
-    const cplx T = e[0];
-    cplx u = fma_rot(v[1], INV ? -T.y : T.y);
-    const cplx ut = mul_mi<INV>(u);
-    fma_bfly(v[0], T.x, half ? ut : u, v[0], v[1]);
+    cplx p, m;
+    fma_bfly_turnable<INV>(v[0], e[0], v[1], half, p, m);
+    v[0] = p;
+    v[1] = m;
   }
 };
 
@@ -403,6 +417,7 @@ __device__ __forceinline__ typename O::V load_input(const BlueGeom& g, const Blu
   }
   if (n >= M) return O::zero();
   cplx y = io.in[h * io.in_stride + off + n];
+  if (MODE == kModeEval && y.x == 0.0 && y.y == 0.0) return O::zero();  // sparse bins: skip the chirp
   if (MODE == kModeRecon && io.add_in) y = cadd(y, io.add_in[h * io.in_stride + off + n]);
   typename O::V x = O::from(y);
   if (MODE == kModeRecon) return O::mul(x, Tab<O>::ws(g)[off + n]);
@@ -521,11 +536,16 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
   __shared__ V nzv[16][kColNz];
   __shared__ int over;
   const V* twP1 = twiddles_of(Tab<O>::twn(g), P1);
+  const bool p1_pow2 = (P1 & (P1 - 1)) == 0;
   auto direct = [&](int b, int k1) {
     V acc = O::zero();
-    for (int q = 0; q < nzc[b]; ++q) acc = O::add(acc, O::mul(nzv[b][q], twP1[(nzi[b][q] * k1) % P1]));
+    for (int q = 0; q < nzc[b]; ++q) {
+      const int e = nzi[b][q] * k1;
+      acc = O::mac(acc, nzv[b][q], twP1[p1_pow2 ? (e & (P1 - 1)) : e % P1]);
+    }
     return acc;
   };
+
   if (MODE == kModeEval) {
     if (threadIdx.x < 16) nzc[threadIdx.x] = 0;
     if (threadIdx.x == 0) over = 0;
@@ -561,10 +581,18 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
     }
     __syncthreads();
     if (!over) {
+      // the sums run column by column across the threads, so that a warp's
+      // loop over the non-zeros of its column does not diverge; the store
+      // then goes row by row through shared memory
+      for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
+        const int b = e / P1, k1 = e - b * P1;
+        sm[k1 * CB + b] = direct(b, k1);
+      }
+      __syncthreads();
       for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
         int k1 = e / CB, b = e - k1 * CB;
         int n2 = n2_0 + b;
-        work[(int64_t)k1 * P2 + n2] = O::mul(direct(b, k1), tw[n2 * k1]);
+        work[(int64_t)k1 * P2 + n2] = O::mul(sm[e], tw[n2 * k1]);
       }
       return;
     }
@@ -782,9 +810,9 @@ __global__ void small_twiddle_kernel(cplx* tw) {
 // and butterfly k < Ns; angles are exact multiples of pi / (4 Ns):
 //   radix 8: w^4 (pi k / Ns, turned past pi / 2), w^2, w, w8 w
 //   radix 4: w^2 (pi k / Ns, turned), w;     radix 2: w (pi k / Ns, turned)
-// (w = exp(-2 pi i k / (R Ns))).  "Turned" entries, 2 k >= Ns, hold i w = s
-// (1 + i t) with s = sin, t = cos / sin of the angle; the others s = cos,
-// t = -tan (cosine > 0 in both).
+// (w = exp(-2 pi i k / (R Ns))).  "Turned" entries, 2 k >= Ns, hold
+// i w = s (1 - i t) as s = sin, t = -cos / sin of the angle; the others
+// w = s (1 + i t) as s = cos, t = -tan (s > 0 in both).
 __global__ void fma_twiddle_kernel(cplx* ft) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kFmaTw) return;
@@ -811,7 +839,7 @@ __global__ void fma_twiddle_kernel(cplx* ft) {
   }
   double sn, cs;
   sincospi(f, &sn, &cs);  // w = cs - i sn
-  ft[i] = turned ? cmake(sn, cs / sn) : cmake(cs, -sn / cs);
+  ft[i] = turned ? cmake(sn, -cs / sn) : cmake(cs, -sn / cs);
 }
 
 // Chirp w[n] = exp(-pi i q / M), q = n^2 mod 2M (exact), as the product of two
