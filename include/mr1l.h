@@ -303,7 +303,11 @@ typedef struct sfft_result {
 /*
  * sfft_dimincr - Algorithm 3 on the GPU.  The detected set and its
  * coefficients (those of the single pass at t = d) are returned in a result
- * owned by the library; release it with sfft_free.
+ * owned by the library; release it with sfft_free.  Within one call the
+ * Bluestein filter spectrum of a lattice size is computed once and reused by
+ * later increments with the same size and Bluestein length (up to 2 GiB of
+ * spectra; the environment variable MR1L_FILTER_CACHE=0 turns this off; the
+ * results are the same bit for bit either way).
  */
 int sfft_dimincr(const sfft_params* params, const sfft_sampler* sampler, void* stream,
                  sfft_result** out);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <atomic>
@@ -158,6 +159,81 @@ static void draw_z(uint64_t seed, int t, int attempt, const std::vector<int>& M,
 // ---------------------------------------------------------------------------
 // Lattice workspace: residues, collisions, coverage, Bluestein tables.
 // ---------------------------------------------------------------------------
+// Filter spectra a run has computed, by (M, P).  A lattice's spectrum depends
+// on its size and the Bluestein length only, and the increments of one run
+// repeat lattice sizes: Algorithm 1 takes the smallest admissible primes above
+// lambda = 2 (|J| - 1), the same list for every increment with as many
+// candidates.  Bounded by kFilterCacheBytes; MR1L_FILTER_CACHE=0 turns it off.
+namespace {
+// Slabs of the filter caches outlive the runs that filled them: a finished
+// run hands its standard-size slabs to this per-device pool and the next run
+// takes them, so a run allocates nothing for its cache once the pool holds
+// enough.
+constexpr size_t kSlabElems = (size_t(256) << 20) / sizeof(cplx);
+constexpr size_t kPoolMaxSlabs = 8;
+std::mutex g_slab_mu;
+std::map<int, std::vector<std::unique_ptr<DevBuf<cplx>>>> g_slab_pool;
+}  // namespace
+
+struct FilterCache {
+  static constexpr size_t kFilterCacheBytes = size_t(2) << 30;
+  std::map<std::pair<int, int>, const cplx*> spectra;
+  // spectra are carved from a few large slabs: one allocation per slab, not
+  // per spectrum (an allocation and its release cost tens of microseconds)
+  std::vector<std::unique_ptr<DevBuf<cplx>>> slabs;
+  size_t slab_used = 0, slab_cap = 0, bytes = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  ~FilterCache() {
+    if (slabs.empty()) return;
+    cudaStreamSynchronize(stream);  // the run's kernels are done with the slabs
+    std::lock_guard<std::mutex> lk(g_slab_mu);
+    auto& pool = g_slab_pool[device];
+    for (auto& sl : slabs)
+      if (sl->n == kSlabElems && pool.size() < kPoolMaxSlabs) pool.push_back(std::move(sl));
+  }
+  std::unique_ptr<DevBuf<cplx>> take_slab(size_t n) {
+    if (n <= kSlabElems) {
+      std::lock_guard<std::mutex> lk(g_slab_mu);
+      auto& pool = g_slab_pool[device];
+      if (!pool.empty()) {
+        auto sl = std::move(pool.back());
+        pool.pop_back();
+        return sl;
+      }
+    }
+    auto sl = std::make_unique<DevBuf<cplx>>();
+    sl->reserve(std::max(n, kSlabElems));
+    return sl;
+  }
+  const cplx* find(int M, int P) const {
+    auto it = spectra.find({M, P});
+    return it == spectra.end() ? nullptr : it->second;
+  }
+  void put(int M, int P, const cplx* src, cudaStream_t s) {
+    const size_t n = (size_t)P, b = n * sizeof(cplx);
+    if (bytes + b > kFilterCacheBytes || spectra.count({M, P})) return;
+    if (slabs.empty()) {
+      stream = s;
+      MR1L_CUDA(cudaGetDevice(&device));
+    }
+    if (slabs.empty() || slab_used + n > slab_cap) {
+      slabs.push_back(take_slab(n));
+      slab_cap = slabs.back()->n;
+      slab_used = 0;
+    }
+    cplx* dst = slabs.back()->get() + slab_used;
+    slab_used += n;
+    MR1L_CUDA(cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToDevice, s));
+    bytes += b;
+    spectra[{M, P}] = dst;
+  }
+  static bool enabled() {
+    const char* e = std::getenv("MR1L_FILTER_CACHE");
+    return !(e && e[0] == '0');
+  }
+};
+
 struct LatticeWork {
   int t = 0, L = 0, Luse = 0;
   std::vector<int> Mh;
@@ -171,6 +247,12 @@ struct LatticeWork {
   DevBuf<int> cover;
   DevBuf<cplx> w, ws, Bh, chirp_seed;
   DevBuf<float4> w_df, ws_df;
+  // filter spectra of the lattices a FilterCache does not hold
+  std::vector<int> sub_Mh;
+  std::vector<int64_t> sub_offh;
+  DevBuf<int> sub_M;
+  DevBuf<int64_t> sub_off;
+  DevBuf<cplx> sub_Bh;
   int df = 0;  // Bluestein butterflies in double-float arithmetic
   BlueGeom geom{};
   LatticeDev dev() {
@@ -224,8 +306,9 @@ struct LatticeWork {
     n_uncovered = hc[1];
   }
 
-  // Chirp and filter tables of lattices 0..Luse-1.
-  void tables(int Luse_, cudaStream_t s) {
+  // Chirp and filter tables of lattices 0..Luse-1; filter spectra found in
+  // cache are copied instead of computed, and new ones are added to it.
+  void tables(int Luse_, cudaStream_t s, FilterCache* cache = nullptr) {
     Luse = Luse_;
     int maxM = 0;
     sumM = 0;
@@ -260,7 +343,47 @@ struct LatticeWork {
     }
     chirp_seed.reserve((size_t)Luse * kChirpSeedLen);
     chirp_tables(geom, maxM, chirp_seed.get(), s);  // writes the double-float copies as well when df
-    blue_filter(geom, s);
+    if (!cache) {
+      blue_filter(geom, s);
+      return;
+    }
+    const size_t pb = (size_t)P * sizeof(cplx);
+    std::vector<int> miss;
+    for (int l = 0; l < Luse; ++l) {
+      if (const cplx* hit = cache->find(Mh[l], P))
+        MR1L_CUDA(cudaMemcpyAsync(Bh.get() + (size_t)l * P, hit, pb, cudaMemcpyDeviceToDevice, s));
+      else
+        miss.push_back(l);
+    }
+    if (miss.empty()) return;
+    if ((int)miss.size() == Luse) {
+      blue_filter(geom, s);
+    } else {
+      // the missing lattices as a geometry of their own (sizes, chirp offsets),
+      // spectra into scratch, then into place
+      const int nm = (int)miss.size();
+      sub_Mh.resize(nm);
+      sub_offh.resize(nm);
+      for (int i = 0; i < nm; ++i) {
+        sub_Mh[i] = Mh[miss[i]];
+        sub_offh[i] = offh[miss[i]];
+      }
+      sub_M.reserve(nm);
+      sub_off.reserve(nm);
+      sub_Bh.reserve((size_t)nm * P);
+      MR1L_CUDA(cudaMemcpyAsync(sub_M.get(), sub_Mh.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+      MR1L_CUDA(cudaMemcpyAsync(sub_off.get(), sub_offh.data(), nm * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      BlueGeom gs = geom;
+      gs.L = nm;
+      gs.M = sub_M.get();
+      gs.off = sub_off.get();
+      gs.Bh = sub_Bh.get();
+      blue_filter(gs, s);
+      for (int i = 0; i < nm; ++i)
+        MR1L_CUDA(cudaMemcpyAsync(Bh.get() + (size_t)miss[i] * P, sub_Bh.get() + (size_t)i * P, pb,
+                                  cudaMemcpyDeviceToDevice, s));
+    }
+    for (int l : miss) cache->put(Mh[l], P, Bh.get() + (size_t)l * P, s);
   }
 };
 
@@ -622,6 +745,7 @@ struct SfftRun {
   int64_t np = 0;
   int tp = 0;
   LatticeWork lw;
+  std::unique_ptr<FilterCache> filter_cache{FilterCache::enabled() ? new FilterCache : nullptr};
   DevBuf<double> anchors;
   DevBuf<cplx> y, C, bins, work, pvals, coef_out;
   DevBuf<uint64_t> keys, keymax;
@@ -874,7 +998,7 @@ struct SfftRun {
       }
       const int covered = lw.n_uncovered == 0;
       const int Luse = covered ? lw.Lneed : Lmax;
-      lw.tables(Luse, s);
+      lw.tables(Luse, s, filter_cache ? filter_cache.get() : nullptr);
       st.L = Luse;
       st.attempts = attempts;
       st.covered = covered;
