@@ -509,6 +509,9 @@ def run_ours(args):
                               "note": "Algorithm 2 passes (Bluestein + gather), algorithmic bytes "
                                       "16*sum_M + 24*|J| per pass; FP64-bound, see roofline"},
         "kernel_share": kernel_share,
+        # summed kernel time of the timed region per step (against ms_per_step:
+        # the share of the step the device spends in kernels)
+        "kernel_ms_per_step": (total_prof_ms / args.steps) if prof and args.workload != "batch256" else None,
         "tile_tuner": tile_summary(P.tune_read()),
         "clocks": clock_info,
         "cpu_baseline": cpu,

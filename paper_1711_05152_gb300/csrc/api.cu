@@ -78,6 +78,30 @@ struct HostRows {
     for (int j = 0; j < tp; ++j) out[j] = pre[p * tp + j];
     if (last) out[tp] = last[q];
   }
+  // the largest component range max_j (max k_j - min k_j) over J: J is the
+  // product prefix x last, so each component ranges over its own factor
+  // (O(np tp + nq), not O(np nq t))
+  int64_t expansion() const {
+    int64_t e = 0;
+    if (np == 0 || nq == 0) return 0;
+    for (int j = 0; j < tp; ++j) {
+      int64_t lo = INT64_MAX, hi = INT64_MIN;
+      for (int64_t p = 0; p < np; ++p) {
+        lo = std::min<int64_t>(lo, pre[p * tp + j]);
+        hi = std::max<int64_t>(hi, pre[p * tp + j]);
+      }
+      e = std::max(e, hi - lo);
+    }
+    if (last) {
+      int64_t lo = INT64_MAX, hi = INT64_MIN;
+      for (int64_t q = 0; q < nq; ++q) {
+        lo = std::min<int64_t>(lo, last[q]);
+        hi = std::max<int64_t>(hi, last[q]);
+      }
+      e = std::max(e, hi - lo);
+    }
+    return e;
+  }
 };
 
 // k -> k mod p componentwise injective on J (membership in P^J)
@@ -86,18 +110,8 @@ static bool injective_mod(const HostRows& J, int64_t p) {
   if (n <= 1) return true;
   const int t = J.t();
   // expansion: a prime above every component range is injective
-  int64_t expansion = 0;
+  if (p > J.expansion()) return true;
   std::vector<int32_t> row(t);
-  std::vector<int64_t> lo(t, INT64_MAX), hi(t, INT64_MIN);
-  for (int64_t c = 0; c < n; ++c) {
-    J.row(c, row.data());
-    for (int j = 0; j < t; ++j) {
-      lo[j] = std::min<int64_t>(lo[j], row[j]);
-      hi[j] = std::max<int64_t>(hi[j], row[j]);
-    }
-  }
-  for (int j = 0; j < t; ++j) expansion = std::max(expansion, hi[j] - lo[j]);
-  if (p > expansion) return true;
   std::vector<std::vector<int64_t>> red(n, std::vector<int64_t>(t));
   for (int64_t c = 0; c < n; ++c) {
     J.row(c, row.data());
@@ -122,19 +136,7 @@ static std::vector<int> prime_set(const HostRows& J, double lam, int Lmax) {
         // once a prime beyond the expansion is reached all larger ones pass
         if (!checked_expansion) {
           checked_expansion = true;
-          int64_t expansion = 0;
-          const int t = J.t();
-          std::vector<int32_t> row(t);
-          std::vector<int64_t> lo(t, INT64_MAX), hi(t, INT64_MIN);
-          for (int64_t c = 0; c < J.n(); ++c) {
-            J.row(c, row.data());
-            for (int j = 0; j < t; ++j) {
-              lo[j] = std::min<int64_t>(lo[j], row[j]);
-              hi[j] = std::max<int64_t>(hi[j], row[j]);
-            }
-          }
-          for (int j = 0; j < t; ++j) expansion = std::max(expansion, hi[j] - lo[j]);
-          expansion_ok_from = expansion + 1;
+          expansion_ok_from = J.expansion() + 1;
         }
       }
       if (ok) {
