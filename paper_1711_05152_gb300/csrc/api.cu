@@ -47,6 +47,84 @@ static int guarded(F&& f) {
 }
 
 // ---------------------------------------------------------------------------
+// The block cache behind DevBuf.  Sizes are rounded up (to 2 MiB from 2 MiB
+// on, to 4 KiB below) so that the buffers of repeated solves of one shape
+// find their blocks again; a request takes the smallest cached block of at
+// least its size and at most twice it.  At most kPoolCacheBytes stay cached
+// per device; an allocation that fails empties the cache and retries.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kPoolCacheBytes = size_t(8) << 30;
+struct BlockPool {
+  std::multimap<size_t, void*> free_blocks;
+  size_t cached = 0;
+};
+std::mutex g_pool_mu;
+// never destroyed: DevBufs with static storage may release after exit-time destructors run
+std::map<int, BlockPool>& pools() {
+  static auto* m = new std::map<int, BlockPool>();
+  return *m;
+}
+size_t pool_round(size_t bytes) {
+  const size_t g = bytes >= (size_t(2) << 20) ? (size_t(2) << 20) : 4096;
+  return (bytes + g - 1) / g * g;
+}
+}  // namespace
+
+void* dev_alloc(size_t bytes, size_t* block_bytes) {
+  const size_t want = pool_round(bytes);
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    BlockPool& bp = pools()[dev];
+    auto it = bp.free_blocks.lower_bound(want);
+    if (it != bp.free_blocks.end() && it->first <= 2 * want) {
+      void* p = it->second;
+      *block_bytes = it->first;
+      bp.cached -= it->first;
+      bp.free_blocks.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    {
+      std::lock_guard<std::mutex> lk(g_pool_mu);
+      BlockPool& bp = pools()[dev];
+      for (auto& kv : bp.free_blocks) cudaFree(kv.second);
+      bp.free_blocks.clear();
+      bp.cached = 0;
+    }
+    MR1L_CUDA(cudaMalloc(&p, want));
+  }
+  *block_bytes = want;
+  return p;
+}
+
+void dev_free(void* p, size_t block_bytes) {
+  if (!p) return;
+  // queued work on any stream may still read the block
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p);
+    return;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    BlockPool& bp = pools()[dev];
+    if (bp.cached + block_bytes <= kPoolCacheBytes) {
+      bp.free_blocks.emplace(block_bytes, p);
+      bp.cached += block_bytes;
+      return;
+    }
+  }
+  cudaFree(p);
+}
+
+// ---------------------------------------------------------------------------
 // Algorithm 1 host logic: Lmax, lambda, the prime set of Eq. 2.2, z draws.
 // ---------------------------------------------------------------------------
 static bool is_prime_u64(int64_t p) {
@@ -166,48 +244,14 @@ static void draw_z(uint64_t seed, int t, int attempt, const std::vector<int>& M,
 // repeat lattice sizes: Algorithm 1 takes the smallest admissible primes above
 // lambda = 2 (|J| - 1), the same list for every increment with as many
 // candidates.  Bounded by kFilterCacheBytes; MR1L_FILTER_CACHE=0 turns it off.
-namespace {
-// Slabs of the filter caches outlive the runs that filled them: a finished
-// run hands its standard-size slabs to this per-device pool and the next run
-// takes them, so a run allocates nothing for its cache once the pool holds
-// enough.
-constexpr size_t kSlabElems = (size_t(256) << 20) / sizeof(cplx);
-constexpr size_t kPoolMaxSlabs = 8;
-std::mutex g_slab_mu;
-std::map<int, std::vector<std::unique_ptr<DevBuf<cplx>>>> g_slab_pool;
-}  // namespace
-
 struct FilterCache {
   static constexpr size_t kFilterCacheBytes = size_t(2) << 30;
   std::map<std::pair<int, int>, const cplx*> spectra;
-  // spectra are carved from a few large slabs: one allocation per slab, not
-  // per spectrum (an allocation and its release cost tens of microseconds)
+  // spectra are carved from a few large slabs: one block per slab, not per
+  // spectrum
+  static constexpr size_t kSlabElems = (size_t(256) << 20) / sizeof(cplx);
   std::vector<std::unique_ptr<DevBuf<cplx>>> slabs;
   size_t slab_used = 0, slab_cap = 0, bytes = 0;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  ~FilterCache() {
-    if (slabs.empty()) return;
-    cudaStreamSynchronize(stream);  // the run's kernels are done with the slabs
-    std::lock_guard<std::mutex> lk(g_slab_mu);
-    auto& pool = g_slab_pool[device];
-    for (auto& sl : slabs)
-      if (sl->n == kSlabElems && pool.size() < kPoolMaxSlabs) pool.push_back(std::move(sl));
-  }
-  std::unique_ptr<DevBuf<cplx>> take_slab(size_t n) {
-    if (n <= kSlabElems) {
-      std::lock_guard<std::mutex> lk(g_slab_mu);
-      auto& pool = g_slab_pool[device];
-      if (!pool.empty()) {
-        auto sl = std::move(pool.back());
-        pool.pop_back();
-        return sl;
-      }
-    }
-    auto sl = std::make_unique<DevBuf<cplx>>();
-    sl->reserve(std::max(n, kSlabElems));
-    return sl;
-  }
   const cplx* find(int M, int P) const {
     auto it = spectra.find({M, P});
     return it == spectra.end() ? nullptr : it->second;
@@ -215,13 +259,10 @@ struct FilterCache {
   void put(int M, int P, const cplx* src, cudaStream_t s) {
     const size_t n = (size_t)P, b = n * sizeof(cplx);
     if (bytes + b > kFilterCacheBytes || spectra.count({M, P})) return;
-    if (slabs.empty()) {
-      stream = s;
-      MR1L_CUDA(cudaGetDevice(&device));
-    }
     if (slabs.empty() || slab_used + n > slab_cap) {
-      slabs.push_back(take_slab(n));
-      slab_cap = slabs.back()->n;
+      slabs.push_back(std::make_unique<DevBuf<cplx>>());
+      slab_cap = std::max(n, kSlabElems);
+      slabs.back()->reserve(slab_cap);
       slab_used = 0;
     }
     cplx* dst = slabs.back()->get() + slab_used;

@@ -46,27 +46,37 @@ void set_last_error(int code, const std::string& msg);
   } while (0)
 
 // ---------------------------------------------------------------------------
-// Device buffer (plain cudaMalloc'd memory owned by a plan or workspace).
+// Device memory of plans and workspaces.  Blocks come from a per-device cache
+// of released blocks (dev_alloc / dev_free, api.cu): a solve allocates and
+// releases dozens of buffers, and cudaMalloc / cudaFree of large blocks cost
+// tens to hundreds of microseconds each while the GPU waits.  dev_free
+// synchronises the device first, as the cudaFree it replaces does, so a cached
+// block is never handed out while queued work may still use it.
 // ---------------------------------------------------------------------------
+void* dev_alloc(size_t bytes, size_t* block_bytes);
+void dev_free(void* p, size_t block_bytes);
+
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  size_t block = 0;  // bytes of the block behind p
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) dev_free(p, block);
     p = nullptr;
     n = 0;
+    block = 0;
   }
   // grow-only: keeps the allocation when it is already large enough
   T* reserve(size_t count) {
     if (count <= n && p) return p;
     release();
     size_t bytes = (count ? count : 1) * sizeof(T);
-    MR1L_CUDA(cudaMalloc(&p, bytes));
+    p = (T*)dev_alloc(bytes, &block);
     n = count;
     return p;
   }
