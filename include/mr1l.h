@@ -20,7 +20,9 @@
  *   - "device" pointers are CUDA global memory of the current device, owned
  *     by the caller; "host" pointers are ordinary host memory, owned by the
  *     caller and only read during the call.  A plan owns its own device
- *     buffers and frees them in mr1l_destroy().
+ *     buffers and frees them in mr1l_destroy().  Freed library buffers go to
+ *     a per-device cache of blocks that later plans and calls reuse (at most
+ *     8 GiB kept; freeing synchronises the device, as cudaFree does).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Transforms are asynchronous on that stream; plan creation
  *     and sfft_dimincr synchronise it.
