@@ -233,6 +233,7 @@ def oracle_sample(name: str, wl, outs) -> dict:
     dt = time.perf_counter() - t0
     scaled = dt * full_samples / max(sample_samples, 1)
     return {"value": full_detected / scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": f"{host_cpu()}, {host_cores()} cores",
             "sample": f"{what}: {sample_samples} of {full_samples} samples in {dt:.1f} s (numpy, one "
                       f"thread), time scaled by samples"}
 
@@ -248,6 +249,19 @@ def _oracle_job(job):
     res = osfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=seed,
                      t_stop=t_stop)
     return res.samples, t0, time.time()
+
+
+def host_cpu() -> str:
+    """The host's CPU model (lscpu's "Model name", else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
 
 
 def host_cores() -> int:
@@ -279,6 +293,7 @@ def oracle_sample_all_cores(name: str, wl, outs, cores: int | None = None, t_sto
     wall = max(r[2] for r in res) - min(r[1] for r in res)
     value = samples / wall * full_detected / max(full_samples, 1)
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "host": f"{host_cpu()}, {host_cores()} cores",
             "sample": f"oracle increments t<={t_stop} of {name} seeds {jobs[0][1]}..{jobs[-1][1]}, one "
                       f"single-threaded process per core: {samples} samples in {wall:.1f} s wall, "
                       f"scaled by the timed job's coefficients per sample"}
@@ -311,7 +326,8 @@ def run_reference(args):
         "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(CONFIG, form="CPU oracle (numpy, pocketfft)"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": f"{host_cpu()}, {host_cores()} cores"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
