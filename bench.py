@@ -2,18 +2,26 @@
 """Benchmark of the dimension-incremental sparse FFT over multiple rank-1
 lattices (Algorithm 3) on GB300.
 
-Workload (one "step" = one complete sparse FFT, every hot-path stage):
-  d = 10, N = 32 (search box [-32, 32]^10), s = 1000 planted frequencies,
-  |c| ~ U[1, 10] with uniform phase, complex Gaussian noise at SNR 40 dB,
-  r = 5 detection iterations, theta = 1e-12 relative, b = 10.
+Headline workload (one "step" = one complete sparse FFT, every hot-path
+stage: 1-D detections, Algorithm 1 lattice searches, sampling, Algorithm 2
+transforms, selections):
+  d = 25, N = 32 (search box [-32, 32]^25), s = 10^4 planted frequencies,
+  |c| log-uniform in [1e-2, 10] with uniform phase, complex Gaussian noise at
+  SNR 20 dB, r = 10 detection iterations fused per increment, theta = 1e-12
+  relative, b = 10 (about 9.7e9 samples per solve).
 
 Prints one JSON line (rank 0).  `value` is detected coefficients per second
 over all ranks with the planted signal resident in HBM; `e2e` is the same
 metric through the host-buffer API.  `roofline` describes the dominant
 kernel (live CUDA-event timing of every library launch during the timed
-region); `cpu_baseline` is the CPU oracle on a bounded sample.
+region), `memory_bound_kernels` the HBM rate of every other kernel;
+`cpu_baseline` is the CPU oracle on a bounded sample.  `secondary` holds the
+d = 10 workload, the 256-signal batch and the differentiable transform, each
+batched and plain.  A solve of the headline workload takes seconds, so the
+timed steps are capped by a time budget (`steps` is the count timed).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload large_d25|plain_d10|batch256|diff]
 """
 
 from __future__ import annotations
@@ -42,7 +50,9 @@ import workloads as W
 
 METRIC = "detected coeffs/sec & lattice-transform HBM GB/s (% peak), batched vs plain, same GB300"
 UNIT = "coeffs/s"
-WORKLOAD = "plain_d10"
+WORKLOAD = "large_d25"
+HEADLINE_BUDGET_S = 50.0    # timed region of the headline form
+SECONDARY_BUDGET_S = 12.0   # each other form and workload
 DESCRIPTIONS = {
     "plain_d10": "plain_d10: d=10, N=32 (box [-32,32]^10), s=1000 planted, |c|~U[1,10] uniform phase, "
                  "SNR 40 dB, r=5, theta=1e-12 relative, b=10",
@@ -59,7 +69,12 @@ FORMS = {
     "batch256": ("batched: 16 signals in flight on their own streams, repetitions fused",
                  "plain: one signal after another on one stream, one repetition per launch sequence"),
 }
-CONFIG = {"workload": DESCRIPTIONS[WORKLOAD]}
+L2_NOTE = "256 MiB buffer written before every timed GPU step (the workloads' arrays also exceed L2)"
+
+
+def config_of(name: str, seed: int) -> dict:
+    """The config object both arms print for a workload."""
+    return {"workload": DESCRIPTIONS[name], "seed": seed, "l2": L2_NOTE}
 
 
 class Workload:
@@ -180,14 +195,16 @@ class ClockSampler:
 
 
 def reduce_scalar(x: float, op: str, world: int, device=None) -> float:
-    """Across ranks: "max" (the slowest rank's time) or "sum" (all ranks'
-    units).  A no-op for one rank; uses the default process group otherwise."""
+    """Across ranks: "max" (the slowest rank's time), "min" (a step count all
+    ranks can run) or "sum" (all ranks' units).  A no-op for one rank; uses
+    the default process group otherwise."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
     t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    ops = {"max": dist.ReduceOp.MAX, "min": dist.ReduceOp.MIN, "sum": dist.ReduceOp.SUM}
+    dist.all_reduce(t, op=ops[op])
     return float(t.item())
 
 
@@ -299,33 +316,70 @@ def oracle_sample_all_cores(name: str, wl, outs, cores: int | None = None, t_sto
                       f"scaled by the timed job's coefficients per sample"}
 
 
+ORACLE_LARGE = os.path.join(ROOT, "tests", "golden", "oracle_large_d25_seed1.npz")
+
+
+def _oracle_full_totals(name: str, seed: int):
+    """(samples, detected) of the oracle's complete run of a workload, when
+    the oracle's stored run exists (written by tests/golden/make_oracle_golden.py)."""
+    if name == "large_d25" and seed == 1 and os.path.exists(ORACLE_LARGE):
+        z = np.load(ORACLE_LARGE)
+        return int(z["samples"]), int(z["freqs"].shape[0])
+    return None
+
+
 def run_reference(args):
+    """The CPU oracle as it stands (numpy, one thread) on the same workload,
+    metric and config.  plain_d10: complete solves.  large_d25: a complete
+    oracle solve takes hours, so each step is the bounded sample of
+    increments t <= 3, and the rate is scaled to the complete job by samples
+    (the oracle's own complete run gives its total samples and detected
+    coefficients).  Steps stop once about 150 s have been spent."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
     from oracle import sfft as osfft
+    name = args.workload if args.workload in ("plain_d10", "large_d25") else WORKLOAD
     tiny, tp = W.workload("tiny_d3", 1)
     for _ in range(args.warmup):
         osfft.sfft(tiny, tp["s"], tp["s_local"], tp["r"], tp["b"], tp["theta"], tp["theta_mode"], seed=1)
-    sig, p = W.workload(WORKLOAD, args.seed)
-    times, detected = [], 0
+    sig, p = W.workload(name, args.seed)
+    t_stop = 3 if name == "large_d25" else None
+    totals = _oracle_full_totals(name, args.seed) if t_stop else None
+    if t_stop and totals is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle's complete run of this workload and "
+                                                              "seed (its sample total) is not stored"}), flush=True)
+        return 0
+    times, detected, samples = [], 0, 0
     budget = 150.0
-    for i in range(args.steps):
+    for _ in range(args.steps):
         t0 = time.perf_counter()
-        res = osfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=args.seed)
+        res = osfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=args.seed,
+                         t_stop=t_stop)
         times.append(time.perf_counter() - t0)
         detected += res.freqs.shape[0]
+        samples += res.samples
         if sum(times) + times[-1] > budget:
             break
     total = sum(times)
-    value = detected / total
-    sample = (f"{len(times)} full plain_d10 oracle solves (of --steps {args.steps}; capped at about "
-              f"{budget:.0f} s); warm-up: {args.warmup} solves of the d=3 workload")
+    if t_stop:
+        full_samples, full_detected = totals
+        value = samples / total * full_detected / full_samples
+        ms_step = 1e3 * total / len(times) * full_samples / (samples / len(times))
+        sample = (f"{len(times)} oracle runs of increments t<={t_stop} of {name} seed {args.seed} (of --steps "
+                  f"{args.steps}; capped at about {budget:.0f} s), {samples // len(times)} of the complete run's "
+                  f"{full_samples} samples each, time scaled by samples; warm-up: {args.warmup} solves of the d=3 "
+                  f"workload")
+    else:
+        value = detected / total
+        ms_step = 1e3 * total / len(times)
+        sample = (f"{len(times)} full {name} oracle solves (of --steps {args.steps}; capped at about "
+                  f"{budget:.0f} s); warm-up: {args.warmup} solves of the d=3 workload")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "steps": len(times), "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(CONFIG, form="CPU oracle (numpy, pocketfft)"),
+        "config": config_of(name, args.seed), "form": "CPU oracle (numpy, pocketfft)",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                          "host": f"{host_cpu()}, {host_cores()} cores"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -354,6 +408,140 @@ def fast_profile(prof) -> dict:
     return out
 
 
+def timed_solves(wl, batched, *, fft="f64", warmup, steps, min_warmup, budget_s, flush, profile=False,
+                 host=False, world=1, dev=None):
+    """W warm-up solves (at least min_warmup; more up to `warmup` while they
+    take under 20 s), then K timed solves with K = min(steps, budget_s / the
+    median warm-up time) (at least 2; the smallest K of all ranks), the L2
+    flushed before each.  Device time from CUDA events around each solve
+    (host=False, inputs resident in HBM) or host wall time around each solve
+    through the host-buffer API (host=True: copies of inputs and results
+    inside the timed region)."""
+    import torch
+
+    import paper_1711_05152_gb300 as P
+    wtimes = []
+    while len(wtimes) < max(min_warmup, 1):
+        t0 = time.perf_counter()
+        wl.solve(batched, host=host, fft=fft)
+        torch.cuda.synchronize()
+        wtimes.append(time.perf_counter() - t0)
+        if len(wtimes) >= min_warmup and (len(wtimes) >= warmup or sum(wtimes) > 20.0):
+            break
+    est = statistics.median(wtimes)
+    k = int(min(steps, max(2, math.floor(budget_s / max(est, 1e-6)))))
+    k = int(reduce_scalar(float(k), "min", world, dev))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if profile:
+        P.prof_reset()
+        P.prof_enable(True)
+    launches0 = P.prof_launches()
+    total_ms, samp_ms, detected, last = 0.0, 0.0, 0, None
+    for _ in range(k):
+        flush.fill_(1)                       # evict L2 between steps (not timed)
+        torch.cuda.synchronize()
+        if host:
+            t0 = time.perf_counter()
+            last = wl.solve(batched, host=True, fft=fft)
+            total_ms += 1e3 * (time.perf_counter() - t0)
+        else:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            last = wl.solve(batched, fft=fft)
+            e1.record()
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        samp_ms += sum(o.ms_sampling for o in last)
+        detected += sum(o.freqs.shape[0] for o in last)
+    launches = P.prof_launches() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    prof = None
+    if profile:
+        P.prof_enable(False)
+        prof = P.prof_read()
+    return dict(ms=reduce_scalar(total_ms, "max", world, dev), detected=reduce_scalar(float(detected), "sum", world, dev),
+                launches=launches, prof=prof, last=last, samp_ms=reduce_scalar(samp_ms, "max", world, dev), steps=k,
+                warmup=len(wtimes))
+
+
+def _rate(m) -> float:
+    return m["detected"] / (m["ms"] / 1e3)
+
+
+def memory_bound_kernels(prof, hbm) -> dict:
+    """Achieved algorithmic GB/s of every kernel that is not a Bluestein FFT
+    pass (live CUDA-event times of the timed region), against the HBM peak."""
+    out = {}
+    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        if k.startswith("blue_") or not v["bytes"] or not v["ms"]:
+            continue
+        gbs = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+        out[k] = {"launches": v["launches"], "ms": round(v["ms"], 4), "GBps": round(gbs, 1),
+                  "frac_of_hbm": round(gbs / hbm, 4), "bytes_per_launch": v["bytes"] / v["launches"]}
+    return out
+
+
+def measure_diff(dev, steps, warmup, budget_s, flush, seed=1) -> dict:
+    """The differentiable transform on 10^5 frequencies in [-64, 64]^20 with
+    64 complex right-hand sides: one step = forward Algorithm 2 plus the
+    backward pass (the ADJOINT kernel path) of ||reconstruct(y) - c||^2
+    through the torch.autograd.Function, device-timed.  The plain form makes
+    one forward and one adjoint call per right-hand side."""
+    import torch
+
+    import paper_1711_05152_gb300 as P
+    from paper_1711_05152_gb300 import autograd as AG
+    I, rng = W.diff_problem(100000, 20, 64, 64, seed=seed)
+    pl = P.plan_search(I, seed=seed + 1)
+    y0 = torch.from_numpy(W.complex_normal(rng, (64, pl.sum_M))).to(dev)
+    c = torch.from_numpy(W.complex_normal(rng, (64, pl.nI))).to(dev)
+
+    def batched():
+        y = y0.detach().requires_grad_(True)
+        loss = (AG.reconstruct(y, pl) - c).abs().pow(2).sum()
+        loss.backward()
+        return y.grad
+
+    def plain():
+        return torch.stack([pl.evaluate(2.0 * (pl.reconstruct(y0[h]) - c[h]), P.MR1L_ADJOINT) for h in range(64)])
+
+    def timed(fn, w, k_max):
+        t_w = []
+        for _ in range(max(w, 1)):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            t_w.append(time.perf_counter() - t0)
+        k = int(min(k_max, max(2, math.floor(budget_s / max(statistics.median(t_w), 1e-6)))))
+        total = 0.0
+        g = None
+        for _ in range(k):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return total / k, k, g
+
+    b_ms, b_k, gb = timed(batched, warmup, steps)
+    p_ms, p_k, gp = timed(plain, 1, steps)
+    diff = float((gb - gp).abs().max() / gp.abs().max())
+    return {"workload": "diff: 10^5 frequencies in [-64,64]^20 (Algorithm 1 lattice, L=%d, sum M=%d), 64 complex "
+                        "right-hand sides; one step = forward + backward of ||reconstruct(y)-c||^2" % (pl.L, pl.sum_M),
+            "value": 64 / (b_ms / 1e3), "unit": "right-hand sides/s (forward + adjoint)", "ms_per_step": b_ms,
+            "steps": b_k, "plain": {"value": 64 / (p_ms / 1e3), "ms_per_step": p_ms, "steps": p_k,
+                                    "form": "one forward and one adjoint call per right-hand side"},
+            "batched_over_plain": p_ms / b_ms, "form": "torch.autograd.Function over all 64 right-hand sides",
+            "max_rel_grad_diff_vs_plain": diff}
+
+
 def run_ours(args):
     import torch
 
@@ -366,67 +554,32 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     P.lib()
-
     seed = args.seed + rank                      # independent signals per GPU (weak scaling)
-    wl = Workload(args.workload, seed, dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    common = dict(flush=flush, world=world, dev=dev)
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+    if args.workload == "diff":
+        d = measure_diff(dev, args.steps, max(args.warmup, 3), HEADLINE_BUDGET_S, flush, seed)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, **d, "n_gpus": world, "warmup": max(args.warmup, 3),
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                              "data": "synthetic", "config": {"workload": d["workload"], "seed": args.seed}}),
+                  flush=True)
+        return 0
 
-    def reduce(x, op):
-        return reduce_scalar(x, op, world, dev)
-
-    def timed(batched, profile, fft="f64"):
-        for _ in range(args.warmup):
-            wl.solve(batched, fft=fft)
-        barrier()
-        torch.cuda.synchronize()
-        if profile:
-            P.prof_reset()
-            P.prof_enable(True)
-        launches0 = P.prof_launches()
-        total_ms, samp_ms, detected, last = 0.0, 0.0, 0, None
-        for _ in range(args.steps):
-            flush.fill_(1)                       # evict L2 between steps (not timed)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            last = wl.solve(batched, fft=fft)
-            e1.record()
-            torch.cuda.synchronize()
-            total_ms += e0.elapsed_time(e1)
-            samp_ms += sum(o.ms_sampling for o in last)
-            detected += sum(o.freqs.shape[0] for o in last)
-        launches = P.prof_launches() - launches0
-        barrier()
-        torch.cuda.synchronize()
-        prof = None
-        if profile:
-            P.prof_enable(False)
-            prof = P.prof_read()
-        return dict(ms=reduce(total_ms, "max"), detected=reduce(float(detected), "sum"), launches=launches,
-                    prof=prof, last=last, samp_ms=reduce(samp_ms, "max"))
-
+    wl = Workload(args.workload, seed, dev)
     clocks = ClockSampler(local)
     clocks.start()
-    bat = timed(True, True)
+    bat = timed_solves(wl, True, warmup=args.warmup, steps=args.steps, min_warmup=3, budget_s=HEADLINE_BUDGET_S,
+                       profile=True, **common)
     clock_info = clocks.stop()
-    plain = timed(False, False)
-    fast = None if args.no_fast_fft else timed(True, True, fft="df")
-
-    # end to end through the host-buffer API (inputs copied in, results copied out)
-    wl.solve(True, host=True)
-    barrier()
-    t0 = time.perf_counter()
-    det_e2e, outs = 0, None
-    for _ in range(args.steps):
-        outs = wl.solve(True, host=True)
-        det_e2e += sum(o.freqs.shape[0] for o in outs)
-    e2e_s = reduce(time.perf_counter() - t0, "max")
-    det_e2e = reduce(float(det_e2e), "sum")
+    sec = SECONDARY_BUDGET_S
+    plain = timed_solves(wl, False, warmup=1, steps=args.steps, min_warmup=1, budget_s=sec, **common)
+    fast = None if args.no_fast_fft else timed_solves(wl, True, fft="df", warmup=1, steps=args.steps, min_warmup=1,
+                                                       budget_s=sec, profile=True, **common)
+    e2e = timed_solves(wl, True, host=True, warmup=1, steps=args.steps, min_warmup=1, budget_s=sec, **common)
     h2d = sum(sig.freqs.size * 4 + sig.coeffs.size * 16 for sig, _ in wl.items)
-    d2h = int(sum(o.freqs.size * 4 + o.coeffs.size * 16 for o in outs))
+    d2h = int(sum(o.freqs.size * 4 + o.coeffs.size * 16 for o in e2e["last"]))
 
     # The batched form of the 256-signal workload runs 16 streams at once, so a
     # kernel's events also cover time its CTAs wait behind other streams; its
@@ -444,14 +597,35 @@ def run_ours(args):
         prof = P.prof_read()
         prof_src = "one extra solve of the single-stream form (the batched form overlaps 16 streams)"
 
+    # the other workloads, batched and plain (and the differentiable transform)
+    secondary = {}
+    if not args.no_secondary:
+        for name in ("plain_d10", "batch256"):
+            if name == args.workload:
+                continue
+            w2 = Workload(name, seed, dev)
+            b2 = timed_solves(w2, True, warmup=3, steps=args.steps, min_warmup=3, budget_s=sec, **common)
+            p2 = timed_solves(w2, False, warmup=1, steps=args.steps, min_warmup=1, budget_s=sec, **common)
+            secondary[name] = {"workload": DESCRIPTIONS[name], "value": _rate(b2), "unit": UNIT,
+                               "ms_per_step": b2["ms"] / b2["steps"], "steps": b2["steps"],
+                               "form": FORMS[name][0], "plain": {"value": _rate(p2), "ms_per_step": p2["ms"] / p2["steps"],
+                                                                 "steps": p2["steps"], "form": FORMS[name][1]},
+                               "batched_over_plain": (p2["ms"] / p2["steps"]) / (b2["ms"] / b2["steps"]),
+                               "support_exact": w2.exact(b2["last"]),
+                               "excluding_sampling": ({"value": b2["detected"] / ((b2["ms"] - b2["samp_ms"]) / 1e3)}
+                                                      if name != "batch256" else None)}
+            del w2
+        secondary["diff"] = measure_diff(dev, args.steps, 3, sec, flush, seed)
+
     if rank != 0:
         return 0
 
     last = bat["last"]
-    value = bat["detected"] / (bat["ms"] / 1e3)
+    value = _rate(bat)
     total_prof_ms = sum(v["ms"] for v in prof.values()) or 1.0
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
     peaks, peak_src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
     roofline = None
     if dom is not None:
         per_launch_ms = dom["ms"] / dom["launches"]
@@ -472,9 +646,8 @@ def run_ours(args):
                         "timed_in": prof_src}
         else:
             achieved = dom["bytes"] / dom["launches"] / (per_launch_ms * 1e-3) / 1e9
-            pk = peaks.get("hbm_gbs", 6800.0)
-            roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": pk, "unit": "GB/s",
-                        "frac": achieved / pk, "traffic": traffic, "peak_source": peak_src,
+            roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                        "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
                         "share_of_kernel_time": dom["ms"] / total_prof_ms, "launches": dom["launches"],
                         "timed_in": prof_src}
 
@@ -486,8 +659,7 @@ def run_ours(args):
         for st in o.steps:
             reps = p["r"] if st["t"] < sig.d else 1
             alg_bytes += reps * (16 * st["sum_M"] + 24 * st["n_cand"])
-    alg_bytes *= args.steps
-    hbm = peaks.get("hbm_gbs", 6800.0)
+    alg_bytes *= bat["steps"] if args.workload != "batch256" else 1
     lat_gbs = alg_bytes / (recon_ms * 1e-3) / 1e9 if recon_ms else None
     kernel_share = {k: round(v["ms"] / total_prof_ms, 4) for k, v in
                     sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]}
@@ -500,47 +672,50 @@ def run_ours(args):
 
     form_b, form_p = FORMS[args.workload]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": bat["ms"] / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": bat["steps"],
+        "steps_requested": args.steps, "warmup": bat["warmup"], "warmup_requested": args.warmup,
+        "ms_per_step": bat["ms"] / bat["steps"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": DESCRIPTIONS[args.workload], "form": form_b,
-                   "l2": "256 MiB buffer written between timed steps",
-                   "parallelism": f"{world} GPU(s), independent signals per GPU", "seed": args.seed},
-        "plain": {"value": plain["detected"] / (plain["ms"] / 1e3), "ms_per_step": plain["ms"] / args.steps,
+        "config": config_of(args.workload, args.seed),
+        "form": form_b, "parallelism": f"{world} GPU(s), independent signals per GPU",
+        "budget": f"timed steps = min(--steps, {HEADLINE_BUDGET_S:.0f} s / the median warm-up solve), at least 2",
+        "plain": {"value": _rate(plain), "ms_per_step": plain["ms"] / plain["steps"], "steps": plain["steps"],
                   "form": form_p},
-        "batched_over_plain": plain["ms"] / bat["ms"] if bat["ms"] else None,
+        "batched_over_plain": (plain["ms"] / plain["steps"]) / (bat["ms"] / bat["steps"]),
         # the paper's runtimes leave out sampling: the same rate with the time of
         # the sampler's kernels (GPU events around them) taken off the step
         "excluding_sampling": ({"value": bat["detected"] / ((bat["ms"] - bat["samp_ms"]) / 1e3),
-                                "ms_per_step": (bat["ms"] - bat["samp_ms"]) / args.steps,
-                                "sampling_ms_per_step": bat["samp_ms"] / args.steps}
+                                "ms_per_step": (bat["ms"] - bat["samp_ms"]) / bat["steps"],
+                                "sampling_ms_per_step": bat["samp_ms"] / bat["steps"]}
                                if args.workload != "batch256" and bat["ms"] > bat["samp_ms"] else None),
         "fast_fft": None if fast is None else {
-            "value": fast["detected"] / (fast["ms"] / 1e3), "ms_per_step": fast["ms"] / args.steps,
+            "value": _rate(fast), "ms_per_step": fast["ms"] / fast["steps"], "steps": fast["steps"],
             "form": "batched, Bluestein butterflies in double-float (FP32 pairs) instead of FP64",
             "same_support_as_f64": all(np.array_equal(a.freqs, b.freqs) for a, b in zip(fast["last"], last)),
             "max_rel_coeff_diff_vs_f64": max((float(np.max(np.abs(a.coeffs - b.coeffs) / np.abs(b.coeffs)))
                                              for a, b in zip(fast["last"], last) if b.coeffs.size and
                                              np.array_equal(a.freqs, b.freqs)), default=None),
             "gpu_launches": int(fast["launches"]), **fast_profile(fast["prof"])},
-        "e2e": {"value": det_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": d2h},
+        "e2e": {"value": _rate(e2e), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
+                "steps": e2e["steps"], "l2": "flushed before every step, as in the device-timed loop"},
         "gpu_launches": int(bat["launches"]),
         "roofline": roofline,
+        "memory_bound_kernels": memory_bound_kernels(prof, hbm),
         "lattice_transform": {"GBps": lat_gbs, "frac_of_hbm": (lat_gbs / hbm) if lat_gbs else None,
-                              "hbm_peak": hbm, "ms_per_step": recon_ms / args.steps,
+                              "hbm_peak": hbm, "ms_per_step": recon_ms / bat["steps"],
                               "note": "Algorithm 2 passes (Bluestein + gather), algorithmic bytes "
                                       "16*sum_M + 24*|J| per pass; FP64-bound, see roofline"},
         "kernel_share": kernel_share,
         # summed kernel time of the timed region per step (against ms_per_step:
         # the share of the step the device spends in kernels)
-        "kernel_ms_per_step": (total_prof_ms / args.steps) if prof and args.workload != "batch256" else None,
+        "kernel_ms_per_step": (total_prof_ms / bat["steps"]) if prof and args.workload != "batch256" else None,
         "tile_tuner": tile_summary(P.tune_read()),
         "clocks": clock_info,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
         "detected": int(sum(o.freqs.shape[0] for o in last)), "support_exact": wl.exact(last),
         "samples": int(sum(o.samples for o in last)),
+        "secondary": secondary or None,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -713,8 +888,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIPTIONS),
-                    help="plain_d10 (default line), large_d25 or batch256")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCRIPTIONS) + ["diff"],
+                    help="large_d25 (default line), plain_d10, batch256, or diff (the differentiable transform)")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads of the default line")
     ap.add_argument("--no-fast-fft", action="store_true", help="skip the double-float FFT form")
     ap.add_argument("--fft", default="f64", choices=["f64", "df"], help="arithmetic of --kernel-case and --paper-table")
     ap.add_argument("--kernel-case", action="store_true",

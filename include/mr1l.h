@@ -65,6 +65,11 @@ extern "C" {
                                    transformations) on the FP32 pipes instead of FP64; inputs,
                                    outputs, chirps, the gather and all decisions stay FP64.
                                    Requires |values| between about 1e-30 and 1e30. */
+#define MR1L_REDRAW 4           /* mr1l_plan_search: the redraw rule of the original construction
+                                   (the remark after Algorithm 1): a lattice whose I_L holds no
+                                   frequency the earlier lattices leave uncovered gets a new z_L
+                                   (Philox counter word attempt + r 2^16 for the r-th new draw),
+                                   at most 64 times, after which the last draw is kept */
 
 /* evaluation modes */
 #define MR1L_EVAL 0
@@ -82,6 +87,21 @@ int mr1l_last_error(char* buf, size_t len);
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int mr1l_version(void);
+
+/* mr1l_pool_stats - the library's cache of device blocks on `device` (every
+ * device buffer of plans and solves comes from it): bytes handed out and not
+ * yet released (outstanding), bytes of released blocks kept for reuse
+ * (cached) and the number of successful cudaMalloc calls so far (mallocs).
+ * Any output may be NULL; a device the library has not used reports zeros.
+ * Host only.  The paper has no counterpart. */
+int mr1l_pool_stats(int device, int64_t* outstanding, int64_t* cached, int64_t* mallocs);
+
+/* mr1l_inject_alloc_failure - a test aid for the error paths: the library's
+ * device allocation request that comes `after` requests from now (0 = the
+ * next one) fails with MR1L_E_NOMEM, as if the device had run out of memory;
+ * -1 cancels a pending injection.  Only the library's host-side allocator is
+ * affected; nothing runs on a GPU.  The paper has no counterpart. */
+int mr1l_inject_alloc_failure(int64_t after);
 
 /*
  * mr1l_plan - plan the transforms on a given multiple rank-1 lattice.
@@ -132,8 +152,10 @@ void mr1l_destroy(mr1l_plan_t* plan);
  *   y  device complex [nrhs][sum_l M_l]: samples p(j z_l / M_l mod 1).
  *   c  device complex [nrhs][nI]: p~_k = (1/counter_k) sum_{l: k in I_l}
  *      (1/M_l) sum_j y_{l,j} exp(-2 pi i j k.z_l / M_l);  0 where counter_k = 0.
- * Each length-M_l DFT runs as a Bluestein convolution over power-of-two FP64
- * FFTs; the gather of the averaged coefficients is fused with the final chirp.
+ * Each length-M_l DFT runs as a Bluestein convolution over FFTs of length 2^k
+ * or 3 * 2^k (the smallest such P >= 2 M_l - 1), in FP64 or, with the plan
+ * flag MR1L_FFT_DF, in double-float butterflies; the gather of the averaged
+ * coefficients is fused with the final chirp.
  */
 int mr1l_reconstruct(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* stream);
 
@@ -177,7 +199,9 @@ int mr1l_evaluate_batch(mr1l_plan_t* const* plans, int count, const void* const*
  *     plan's Bluestein length, the smallest 2^k or 3 * 2^k >= 2 max M_l - 1).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  With CUDA's default lazy module loading,
+ *     that first call may also load the library's device code on the device
+ *     and commit the array's 32 MiB there; later calls allocate nothing.
  *   - Every call shares the one array: calls whose work overlaps on the GPU
  *     (other streams, other host threads) race and must be serialised by the
  *     caller.  No part of the array needs to start at zero.
@@ -270,6 +294,8 @@ typedef struct sfft_params {
                                the paper remarks on in Section 3 for coefficients whose real
                                parts (or imaginary parts) all share one sign, meant for r = 1;
                                the lattices are still drawn (Algorithm 1) */
+    int redraw;             /* 1: Algorithm 1 with the redraw rule of the remark after it (see
+                               MR1L_REDRAW); 0: Algorithm 1 as printed */
 } sfft_params;
 
 #define SFFT_MAX_STEPS 256
@@ -315,6 +341,26 @@ int sfft_dimincr(const sfft_params* params, const sfft_sampler* sampler, void* s
                  sfft_result** out);
 
 void sfft_free(sfft_result* res);
+
+/*
+ * sfft_select - the thresholded "(up to) s-largest" selection of Algorithm 3
+ * (steps 1, 2a and 2e) on its own, over nrhs segments of n values each.
+ *   p        device complex [nrhs][n]: the values p~_k of one pass per segment.
+ *   eligible device uint8 [n] or NULL: 0 marks an index that is never selected
+ *            (a candidate no lattice covers); NULL: all eligible.
+ *   cap      keep at most cap indices per segment (0: none).
+ *   theta    threshold: key >= theta^2 (SFFT_THETA_ABS) or key >= theta^2 times
+ *            the segment's largest eligible key (SFFT_THETA_REL), with key =
+ *            re*re + im*im rounded per operation (no fused multiply-add).
+ *   flags    device uint8 [n]: set to 1 at every index some segment selects
+ *            (the union over segments, as Algorithm 3 unites its passes);
+ *            entries not selected are left as they are.
+ * Within a segment the largest keys win and equal keys go to the smaller
+ * index.  Asynchronous on `stream`; its scratch comes from the block cache,
+ * whose release synchronises the device.
+ */
+int sfft_select(const void* p, int64_t n, int nrhs, const uint8_t* eligible, int64_t cap, double theta,
+                int theta_mode, uint8_t* flags, void* stream);
 
 /*
  * sfft_theorem_params - the parameters of the theorem in Section 4 that

@@ -122,11 +122,19 @@ class MultiLattice:
         return 1 - self.L + int(sum(self.M))
 
 
+REDRAW_CAP = 64   # replacement draws per lattice in the redraw rule
+
+
 def construct(J: np.ndarray, seed: int, t: int, attempt: int, c: float = 2.0,
-              gamma: float = 0.5) -> MultiLattice:
+              gamma: float = 0.5, redraw: bool = False) -> MultiLattice:
     """One run of Algorithm 1 on J (rows in Z^t): primes from Eq. (2.2); for
     L = 1..Lmax draw z_L uniformly in [1, M_L - 1]^t, determine I_L, update the
-    covered set and stop once it equals J."""
+    covered set and stop once it equals J.
+
+    redraw=True applies the rule of the original construction that the remark
+    after Algorithm 1 describes: while the new I_L holds no frequency that
+    the earlier lattices leave uncovered, z_L is drawn again (at most
+    REDRAW_CAP times; after that the last draw is kept)."""
     n = J.shape[0]
     Lmax, lam = lmax_lambda(n, c, gamma)
     primes = prime_set(J, lam, Lmax)
@@ -134,8 +142,13 @@ def construct(J: np.ndarray, seed: int, t: int, attempt: int, c: float = 2.0,
     Ms, zs, us = [], [], []
     for L in range(1, Lmax + 1):
         M = primes[L - 1]
-        z = philox.zvec(seed, t, L - 1, attempt, M)
-        IL = unique_mask(J, z, M)
+        r = 0
+        while True:
+            z = philox.zvec(seed, t, L - 1, attempt, M, redraw=r)
+            IL = unique_mask(J, z, M)
+            if not redraw or (IL & ~covered).any() or r == REDRAW_CAP:
+                break
+            r += 1
         covered |= IL
         Ms.append(M)
         zs.append(z)
@@ -146,13 +159,14 @@ def construct(J: np.ndarray, seed: int, t: int, attempt: int, c: float = 2.0,
 
 
 def search(J: np.ndarray, seed: int, t: int, b: int = 10, c: float = 2.0,
-           gamma: float = 0.5) -> MultiLattice:
+           gamma: float = 0.5, redraw: bool = False) -> MultiLattice:
     """Step 2b of Algorithm 3: Algorithm 1 with c = 2, gamma = 0.5, repeated
     until condition (2.1) holds, b searches in total.  After b failed searches
-    the last one is used; its uncovered candidates get no coefficient."""
+    the last one is used; its uncovered candidates get no coefficient.
+    redraw: the redraw rule (see construct)."""
     ml = None
     for attempt in range(b):
-        ml = construct(J, seed, t, attempt, c, gamma)
+        ml = construct(J, seed, t, attempt, c, gamma, redraw)
         if ml.covered:
             return ml
     return ml

@@ -82,11 +82,13 @@ def uniform(seed: int, purpose: int, t: int, c0, c1, c2) -> np.ndarray:
     return (a >> np.uint64(11)).astype(np.float64) * TWO_M53
 
 
-def zvec(seed: int, t: int, lattice: int, attempt: int, M: int) -> np.ndarray:
+def zvec(seed: int, t: int, lattice: int, attempt: int, M: int, redraw: int = 0) -> np.ndarray:
     """Generating vector z in [1, M-1]^t of lattice `lattice` (0-based) of the
-    given attempt at dimension increment t (Algorithm 1, random choice of z)."""
+    given attempt at dimension increment t (Algorithm 1, random choice of z).
+    redraw r > 0 is the r-th replacement draw of the redraw rule (the remark
+    after Algorithm 1): counter word c2 = attempt + r 2^16."""
     j = np.arange(t, dtype=np.uint64)
-    a, _ = _u64pair(seed, ZVEC, t, j, lattice, attempt)
+    a, _ = _u64pair(seed, ZVEC, t, j, lattice, attempt + (redraw << 16))
     return (np.uint64(1) + a % np.uint64(M - 1)).astype(np.int64)
 
 

@@ -228,12 +228,36 @@ def candidates(prefix: np.ndarray, last: np.ndarray) -> np.ndarray:
     return J
 
 
+def lattice_pass(sig, t: int, seed: int, i: int, J: np.ndarray, ml: lattice.MultiLattice,
+                 cap: int, theta: float, theta_mode: str, eligible: np.ndarray, dft: str = "fft",
+                 zero_anchors: bool = False):
+    """Steps 2c-2e of Algorithm 3 for detection iteration i: sample p along
+    the multiple rank-1 lattice (anchor x'_{t+1..d} of pass i), reconstruct
+    every p~_k by Algorithm 2 and select the (up to) cap largest above the
+    threshold.  Returns (p~, Selection)."""
+    x = anchor(seed, philox.ANCHOR_LAT, t, sig.d, i, zero_anchors)
+    ys = sample_lattice(sig, t, ml, x, dft)
+    if sig.sigma > 0:
+        ys = [y + e for y, e in zip(ys, lattice_noise(seed, t, i, ml, sig.sigma))]
+    p, _ = lattice.reconstruct(J, ml, ys, dft)
+    return p, select(p, cap, theta, theta_mode, eligible)
+
+
+def _lattice_pass_job(args):
+    return lattice_pass(*args)
+
+
 def sfft(sig, s: int, s_local: int, r: int, b: int, theta: float, theta_mode: str,
-         seed: int, dft: str = "fft", t_stop: int | None = None, zero_anchors: bool = False) -> SfftResult:
+         seed: int, dft: str = "fft", t_stop: int | None = None, zero_anchors: bool = False,
+         rep_map=map, redraw: bool = False) -> SfftResult:
     """Algorithm 3.  t_stop (optional) ends the run after that dimension
     increment (a bounded sample of the work; the result is then the
     projected set I^(1..t_stop)).  zero_anchors: every anchor x' is 0 (the
-    deterministic variant of the remark in Section 3)."""
+    deterministic variant of the remark in Section 3).  rep_map applies the
+    independent detection iterations of an increment (default: the builtin
+    map, one after another; a process pool's map runs them side by side with
+    the same arithmetic).  redraw: Algorithm 1 with the redraw rule of the
+    remark after it (see lattice.construct)."""
     d = sig.d
     if d < 2:
         raise ValueError("the dimension-incremental method needs d >= 2")
@@ -259,17 +283,12 @@ def sfft(sig, s: int, s_local: int, r: int, b: int, theta: float, theta_mode: st
             steps.append(StepStats(t, It.size, 0, 0, 0, 0, True, step_samples, gr, gt))
             samples += step_samples
             continue
-        ml = lattice.search(J, seed, t, b)
+        ml = lattice.search(J, seed, t, b, redraw=redraw)
         eligible = ml.counter() > 0
         detected = np.zeros(n, dtype=bool)
         p = None
-        for i in range(rt):
-            x = anchor(seed, philox.ANCHOR_LAT, t, d, i, zero_anchors)
-            ys = sample_lattice(sig, t, ml, x, dft)
-            if sig.sigma > 0:
-                ys = [y + e for y, e in zip(ys, lattice_noise(seed, t, i, ml, sig.sigma))]
-            p, _ = lattice.reconstruct(J, ml, ys, dft)
-            sel = select(p, st, theta, theta_mode, eligible)
+        jobs = [(sig, t, seed, i, J, ml, st, theta, theta_mode, eligible, dft, zero_anchors) for i in range(rt)]
+        for p, sel in rep_map(_lattice_pass_job, jobs):
             detected[sel.chosen] = True
             gr, gt = min(gr, sel.gap_rank), min(gt, sel.gap_thr)
             step_samples += ml.nodes()

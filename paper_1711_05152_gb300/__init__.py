@@ -31,6 +31,7 @@ MR1L_E_SAMPLER = 5
 MR1L_E_TIMEOUT = 6
 MR1L_STRICT = 1
 MR1L_FFT_DF = 2
+MR1L_REDRAW = 4
 MR1L_EVAL = 0
 MR1L_ADJOINT = 1
 SFFT_THETA_ABS = 0
@@ -44,7 +45,8 @@ EXPORTS = [
     "mr1l_plan_masks", "mr1l_destroy", "mr1l_reconstruct", "mr1l_evaluate", "sfft_dimincr",
     "sfft_free", "sfft_dimincr_batch", "mr1l_reconstruct_noalloc", "mr1l_lattice_noise", "mr1l_prof_enable", "mr1l_prof_reset", "mr1l_prof_launches", "mr1l_prof_read",
     "mr1l_tune_enable", "mr1l_tune_reset", "mr1l_tune_read", "sfft_theorem_params",
-    "mr1l_reconstruct_batch", "mr1l_evaluate_batch",
+    "mr1l_reconstruct_batch", "mr1l_evaluate_batch", "mr1l_pool_stats", "mr1l_inject_alloc_failure",
+    "sfft_select",
 ]
 
 
@@ -89,7 +91,7 @@ class sfft_params(C.Structure):
     _fields_ = [("d", C.c_int), ("N", C.c_int), ("s", C.c_int64), ("s_local", C.c_int64),
                 ("r", C.c_int), ("b", C.c_int), ("theta", C.c_double), ("theta_mode", C.c_int),
                 ("seed", C.c_uint64), ("batch_reps", C.c_int), ("fft_arith", C.c_int), ("t_stop", C.c_int),
-                ("zero_anchors", C.c_int)]
+                ("zero_anchors", C.c_int), ("redraw", C.c_int)]
 
 
 class sfft_step_stats(C.Structure):
@@ -152,6 +154,9 @@ def lib() -> C.CDLL:
     L.mr1l_tune_enable.argtypes = [C.c_int]
     L.mr1l_tune_reset.argtypes = []
     L.mr1l_tune_read.argtypes = [C.c_char_p, C.c_size_t]
+    L.mr1l_pool_stats.argtypes = [C.c_int, i64p, i64p, i64p]
+    L.mr1l_inject_alloc_failure.argtypes = [C.c_int64]
+    L.sfft_select.argtypes = [vp, C.c_int64, C.c_int, vp, C.c_int64, C.c_double, C.c_int, vp, vp]
     _lib = L
     return L
 
@@ -184,6 +189,20 @@ def _i64(a) -> np.ndarray:
 
 def _ptr(a: np.ndarray, ctype):
     return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def check_out(out, shape, device, name: str = "out"):
+    """An output tensor the library will write through a raw pointer: it must
+    be a contiguous complex128 tensor of exactly `shape` on `device` (the
+    input's device), or the kernels would write out of bounds or to another
+    device's memory."""
+    import torch
+    if out.dtype != torch.complex128 or not out.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous complex128 tensor")
+    if tuple(out.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(out.shape)}, expected {tuple(shape)}")
+    if out.device != device:
+        raise ValueError(f"{name} is on {out.device}, expected {device}")
 
 
 class Plan:
@@ -229,6 +248,10 @@ class Plan:
         nrhs = y2.shape[0]
         if out is None:
             out = torch.empty((nrhs, self.nI), dtype=torch.complex128, device=y.device)
+        else:
+            if squeeze and out.dim() == 1:
+                out = out.unsqueeze(0)
+            check_out(out, (nrhs, self.nI), y.device)
         _check(lib().mr1l_reconstruct(self._h, C.c_void_p(y2.data_ptr()), nrhs, C.c_void_p(out.data_ptr()),
                                       C.c_void_p(_stream(stream))))
         return out[0] if squeeze else out
@@ -241,8 +264,7 @@ class Plan:
         y2 = y.reshape(-1, self.sum_M)
         if y2.dtype != torch.complex128 or not y2.is_cuda or not y2.is_contiguous():
             raise TypeError("y must be a contiguous complex128 CUDA tensor")
-        if out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous():
-            raise TypeError("out must be a contiguous complex128 CUDA tensor")
+        check_out(out, (y2.shape[0], self.nI), y.device)
         _check(lib().mr1l_reconstruct_noalloc(self._h, C.c_void_p(y2.data_ptr()), y2.shape[0],
                                               C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream))))
         return out
@@ -258,6 +280,10 @@ class Plan:
         nrhs = c2.shape[0]
         if out is None:
             out = torch.empty((nrhs, self.sum_M), dtype=torch.complex128, device=c.device)
+        else:
+            if squeeze and out.dim() == 1:
+                out = out.unsqueeze(0)
+            check_out(out, (nrhs, self.sum_M), c.device)
         _check(lib().mr1l_evaluate(self._h, C.c_void_p(c2.data_ptr()), nrhs, C.c_void_p(out.data_ptr()),
                                    mode, C.c_void_p(_stream(stream))))
         return out[0] if squeeze else out
@@ -274,10 +300,10 @@ class Plan:
             pass
 
 
-def _flags(strict: bool, fft: str) -> int:
+def _flags(strict: bool, fft: str, redraw: bool = False) -> int:
     if fft not in ("f64", "df"):
         raise ValueError('fft must be "f64" or "df"')
-    return (MR1L_STRICT if strict else 0) | (MR1L_FFT_DF if fft == "df" else 0)
+    return (MR1L_STRICT if strict else 0) | (MR1L_FFT_DF if fft == "df" else 0) | (MR1L_REDRAW if redraw else 0)
 
 
 def plan(I, M, z, strict: bool = False, fft: str = "f64", stream=None) -> Plan:
@@ -296,14 +322,15 @@ def plan(I, M, z, strict: bool = False, fft: str = "f64", stream=None) -> Plan:
 
 
 def plan_search(I, seed: int, c: float = 2.0, gamma: float = 0.5, b: int = 10, strict: bool = False,
-                fft: str = "f64", stream=None) -> Plan:
-    """Plan on a lattice built by Algorithm 1 (up to b searches)."""
+                fft: str = "f64", redraw: bool = False, stream=None) -> Plan:
+    """Plan on a lattice built by Algorithm 1 (up to b searches); redraw:
+    the redraw rule of the remark after Algorithm 1 (MR1L_REDRAW)."""
     I = _i32(I)
     if I.ndim == 1:
         I = I.reshape(-1, 1)
     n, t = I.shape
     h = C.c_void_p()
-    _check(lib().mr1l_plan_search(_ptr(I, C.c_int32), n, t, c, gamma, b, seed, _flags(strict, fft),
+    _check(lib().mr1l_plan_search(_ptr(I, C.c_int32), n, t, c, gamma, b, seed, _flags(strict, fft, redraw),
                                   C.c_void_p(_stream(stream)), C.byref(h)))
     return Plan(h.value, n, t)
 
@@ -322,17 +349,18 @@ def sfft_dimincr(d: int, N: int, s: int, r: int, theta: float, theta_mode: str =
                  s_local: int | None = None, b: int = 10, freqs=None, coeffs=None, sigma: float = 0.0,
                  noise_seed: int | None = None, sampler=None, batch_reps: bool = False,
                  t_stop: int | None = None, fft: str = "f64", zero_anchors: bool = False,
-                 function=None, stream=None) -> SfftOutput:
+                 function=None, redraw: bool = False, stream=None) -> SfftOutput:
     """Algorithm 3.  Either a planted polynomial (freqs [s, d], coeffs [s],
     sigma) evaluated by the library, the Section 5.3 B-spline function
     (``function`` with .groups and .orders, evaluated by the library), or
     ``sampler(req, y_ptr, stream_ptr)``, a Python callable that fills the
     device buffer y_ptr for a request.
-    zero_anchors: the deterministic variant (anchors 0, see sfft_params)."""
+    zero_anchors: the deterministic variant (anchors 0, see sfft_params).
+    redraw: Algorithm 1 with the redraw rule of the remark after it."""
     p = sfft_params(d=d, N=N, s=s, s_local=s if s_local is None else s_local, r=r, b=b, theta=theta,
                     theta_mode=SFFT_THETA_REL if theta_mode == "rel" else SFFT_THETA_ABS, seed=seed,
                     batch_reps=1 if batch_reps else 0, fft_arith=1 if fft == "df" else 0, t_stop=t_stop or 0,
-                    zero_anchors=1 if zero_anchors else 0)
+                    zero_anchors=1 if zero_anchors else 0, redraw=1 if redraw else 0)
     keep = []
     nseed = seed if noise_seed is None else noise_seed
     if function is not None:
@@ -391,7 +419,7 @@ def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[Sfft
     (a planted polynomial: host arrays, or contiguous int32 / complex128 CUDA
     tensors) or function (the Section 5.3 B-spline function, see
     sfft_dimincr), and optionally sigma, s_local, b, noise_seed, batch_reps,
-    fft, zero_anchors."""
+    fft, zero_anchors, redraw."""
     n = len(problems)
     params = (sfft_params * max(n, 1))()
     samps = (sfft_sampler * max(n, 1))()
@@ -403,7 +431,8 @@ def sfft_dimincr_batch(problems: list[dict], concurrency: int = 16) -> list[Sfft
                                 theta_mode=SFFT_THETA_REL if q.get("theta_mode", "rel") == "rel" else SFFT_THETA_ABS,
                                 seed=q["seed"], batch_reps=1 if q.get("batch_reps", True) else 0,
                                 fft_arith=1 if q.get("fft", "f64") == "df" else 0,
-                                zero_anchors=1 if q.get("zero_anchors", False) else 0)
+                                zero_anchors=1 if q.get("zero_anchors", False) else 0,
+                                redraw=1 if q.get("redraw", False) else 0)
         if q.get("function") is not None:
             samps[i] = _bspline_sampler(d, q["function"], keep)
             continue
@@ -438,6 +467,47 @@ def lattice_noise(seed: int, t: int, rep: int, M, sigma: float, stream=None):
     _check(lib().mr1l_lattice_noise(seed, t, rep, M.shape[0], _ptr(M, C.c_int64), sigma,
                                     C.c_void_p(y.data_ptr()), C.c_void_p(_stream(stream))))
     return y
+
+
+def select(p, cap: int, theta: float, theta_mode: str = "rel", eligible=None, flags=None, stream=None):
+    """sfft_select: the thresholded "(up to) cap largest" selection of
+    Algorithm 3 over the rows of p (complex128 CUDA [nrhs, n]); returns the
+    uint8 flags [n] (1 where some row selects the index; OR-ed into `flags`
+    when given)."""
+    import torch
+    p2 = p.reshape(-1, p.shape[-1]) if p.dim() > 0 else p
+    if p2.dtype != torch.complex128 or not p2.is_cuda or not p2.is_contiguous():
+        raise TypeError("p must be a contiguous complex128 CUDA tensor")
+    n = p2.shape[1]
+    if flags is None:
+        flags = torch.zeros(n, dtype=torch.uint8, device=p.device)
+    elif flags.dtype != torch.uint8 or tuple(flags.shape) != (n,) or flags.device != p.device or \
+            not flags.is_contiguous():
+        raise ValueError(f"flags must be a contiguous uint8 tensor of shape ({n},) on {p.device}")
+    el = None
+    if eligible is not None:
+        if eligible.dtype != torch.uint8 or tuple(eligible.shape) != (n,) or eligible.device != p.device or \
+                not eligible.is_contiguous():
+            raise ValueError(f"eligible must be a contiguous uint8 tensor of shape ({n},) on {p.device}")
+        el = C.c_void_p(eligible.data_ptr())
+    _check(lib().sfft_select(C.c_void_p(p2.data_ptr()), n, p2.shape[0], el, cap, theta,
+                             SFFT_THETA_REL if theta_mode == "rel" else SFFT_THETA_ABS, C.c_void_p(flags.data_ptr()),
+                             C.c_void_p(_stream(stream))))
+    return flags
+
+
+def pool_stats(device: int = 0) -> dict:
+    """The library's device block cache on `device`: {"outstanding", "cached",
+    "mallocs"} (see mr1l_pool_stats)."""
+    o, c, m = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().mr1l_pool_stats(device, C.byref(o), C.byref(c), C.byref(m)))
+    return {"outstanding": o.value, "cached": c.value, "mallocs": m.value}
+
+
+def inject_alloc_failure(after: int) -> None:
+    """Test aid: the library's device allocation request `after` requests from
+    now fails with MR1L_E_NOMEM (-1 cancels; see mr1l_inject_alloc_failure)."""
+    _check(lib().mr1l_inject_alloc_failure(after))
 
 
 def prof_enable(on: bool = True) -> None:

@@ -57,7 +57,9 @@ namespace {
 constexpr size_t kPoolCacheBytes = size_t(8) << 30;
 struct BlockPool {
   std::multimap<size_t, void*> free_blocks;
-  size_t cached = 0;
+  size_t cached = 0;       // bytes of the free blocks
+  size_t outstanding = 0;  // bytes of blocks handed out and not yet released
+  int64_t mallocs = 0;     // cudaMalloc calls that succeeded
 };
 std::mutex g_pool_mu;
 // never destroyed: DevBufs with static storage may release after exit-time destructors run
@@ -69,12 +71,32 @@ size_t pool_round(size_t bytes) {
   const size_t g = bytes >= (size_t(2) << 20) ? (size_t(2) << 20) : 4096;
   return (bytes + g - 1) / g * g;
 }
+// allocation requests still to pass before an injected failure (-1: none)
+std::atomic<int64_t> g_fail_after{-1};
+
+// Makes `dev` current for the lifetime of the guard (if it is not already).
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess) prev = cur;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 }  // namespace
 
-void* dev_alloc(size_t bytes, size_t* block_bytes) {
+void* dev_alloc(size_t bytes, size_t* block_bytes, int* device) {
   const size_t want = pool_round(bytes);
   int dev = 0;
   MR1L_CUDA(cudaGetDevice(&dev));
+  *device = dev;
+  int64_t k = g_fail_after.load();
+  while (k >= 0 && !g_fail_after.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 0)
+    throw Error(MR1L_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected failure)");
   {
     std::lock_guard<std::mutex> lk(g_pool_mu);
     BlockPool& bp = pools()[dev];
@@ -83,6 +105,7 @@ void* dev_alloc(size_t bytes, size_t* block_bytes) {
       void* p = it->second;
       *block_bytes = it->first;
       bp.cached -= it->first;
+      bp.outstanding += it->first;
       bp.free_blocks.erase(it);
       return p;
     }
@@ -100,26 +123,27 @@ void* dev_alloc(size_t bytes, size_t* block_bytes) {
     MR1L_CUDA(cudaMalloc(&p, want));
   }
   *block_bytes = want;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  BlockPool& bp = pools()[dev];
+  bp.outstanding += want;
+  ++bp.mallocs;
   return p;
 }
 
-void dev_free(void* p, size_t block_bytes) {
+void dev_free(void* p, size_t block_bytes, int device) {
   if (!p) return;
-  // queued work on any stream may still read the block
-  if (cudaDeviceSynchronize() != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(p);
+  // the block's own device: its queued work may still read the block, and its
+  // cache is the one that may hand the block out again
+  DeviceGuard guard(device);
+  const bool idle = cudaDeviceSynchronize() == cudaSuccess;
+  if (!idle) cudaGetLastError();
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  BlockPool& bp = pools()[device];
+  bp.outstanding -= std::min(bp.outstanding, block_bytes);
+  if (idle && bp.cached + block_bytes <= kPoolCacheBytes) {
+    bp.free_blocks.emplace(block_bytes, p);
+    bp.cached += block_bytes;
     return;
-  }
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) {
-    std::lock_guard<std::mutex> lk(g_pool_mu);
-    BlockPool& bp = pools()[dev];
-    if (bp.cached + block_bytes <= kPoolCacheBytes) {
-      bp.free_blocks.emplace(block_bytes, p);
-      bp.cached += block_bytes;
-      return;
-    }
   }
   cudaFree(p);
 }
@@ -149,6 +173,10 @@ struct HostRows {
   int64_t np;
   const int32_t* last;  // may be null
   int64_t nq;
+  // >= 0: a known upper bound on the component ranges, used instead of
+  // scanning the rows (pre may then be null while no prime at or below the
+  // bound needs the explicit injectivity test)
+  int64_t range_bound = -1;
   int t() const { return tp + (last ? 1 : 0); }
   int64_t n() const { return np * nq; }
   void row(int64_t c, int32_t* out) const {
@@ -162,6 +190,7 @@ struct HostRows {
   int64_t expansion() const {
     int64_t e = 0;
     if (np == 0 || nq == 0) return 0;
+    if (range_bound >= 0) return range_bound;
     for (int j = 0; j < tp; ++j) {
       int64_t lo = INT64_MAX, hi = INT64_MIN;
       for (int64_t p = 0; p < np; ++p) {
@@ -227,11 +256,15 @@ static std::vector<int> prime_set(const HostRows& J, double lam, int Lmax) {
   return out;
 }
 
-static void draw_z(uint64_t seed, int t, int attempt, const std::vector<int>& M, std::vector<int64_t>& z) {
+// z_l of a search: Philox counter (j, l, attempt + r_l 2^16, 3 << 24 | t),
+// r_l the replacement draw of lattice l under the redraw rule (0 otherwise)
+static void draw_z(uint64_t seed, int t, int attempt, const std::vector<int>& M, std::vector<int64_t>& z,
+                   const std::vector<int>* redraws = nullptr) {
   z.assign(M.size() * t, 0);
   for (size_t l = 0; l < M.size(); ++l)
     for (int j = 0; j < t; ++j) {
-      U64Pair u = philox_u64(seed, kZvec, (uint32_t)t, (uint32_t)j, (uint32_t)l, (uint32_t)attempt);
+      const uint32_t c2 = (uint32_t)attempt + (redraws ? (uint32_t)(*redraws)[l] << 16 : 0u);
+      U64Pair u = philox_u64(seed, kZvec, (uint32_t)t, (uint32_t)j, (uint32_t)l, c2);
       z[l * t + j] = 1 + (int64_t)(u.a % (uint64_t)(M[l] - 1));
     }
 }
@@ -277,12 +310,29 @@ struct FilterCache {
   }
 };
 
+struct Staging;
+static void stage_h2d(Staging* st, void* dst, const void* src, size_t bytes, cudaStream_t s);
+static void stage_reset(Staging* st);
+// the coverage result of a search: [0] Lneed, [1] uncovered, [2 + l] |I_l|,
+// [kCoverFirst + l] candidates whose first collision-free lattice is l
+constexpr int kCoverFirst = 2 + 64, kCoverInts = 2 + 128;
+
 struct LatticeWork {
   int t = 0, L = 0, Luse = 0;
+  Staging* stage = nullptr;  // pinned staging of the host-to-device copies (optional)
+  int* cover_host = nullptr;  // pinned [2] for the coverage result (optional)
   std::vector<int> Mh;
   std::vector<int64_t> zh, offh;
   int64_t words = 0, sumM_all = 0, sumM = 0;
   int Lneed = 0, n_uncovered = 0;
+  std::vector<int64_t> I_size;       // |I_l| per lattice
+  std::vector<int64_t> first_count;  // candidates whose first collision-free lattice is l
+  // sum of |I_l| over the lattices in use (pairs (k, l) with k in I_l)
+  int64_t pairs() const {
+    int64_t p = 0;
+    for (int l = 0; l < Luse && l < (int)I_size.size(); ++l) p += I_size[l];
+    return p;
+  }
   DevBuf<int> M;
   DevBuf<int64_t> z, off, bm_off;
   DevBuf<uint32_t> pre_res, last_res, seen;
@@ -330,23 +380,26 @@ struct LatticeWork {
     z.reserve((size_t)L * t);
     off.reserve(L);
     bm_off.reserve(L);
-    MR1L_CUDA(cudaMemcpyAsync(M.get(), Mh.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
-    MR1L_CUDA(cudaMemcpyAsync(z.get(), zh.data(), (size_t)L * t * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    MR1L_CUDA(cudaMemcpyAsync(off.get(), offh.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    MR1L_CUDA(cudaMemcpyAsync(bm_off.get(), bm.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    stage_h2d(stage, M.get(), Mh.data(), L * sizeof(int), s);
+    stage_h2d(stage, z.get(), zh.data(), (size_t)L * t * sizeof(int64_t), s);
+    stage_h2d(stage, off.get(), offh.data(), L * sizeof(int64_t), s);
+    stage_h2d(stage, bm_off.get(), bm.data(), L * sizeof(int64_t), s);
     pre_res.reserve((size_t)L * std::max<int64_t>(J.np, 1));
     last_res.reserve((size_t)L * std::max<int64_t>(J.nq, 1));
     seen.reserve(2 * words);
     umask.reserve(std::max<int64_t>(J.n(), 1));
-    cover.reserve(2);
+    cover.reserve(kCoverInts);
     MR1L_CUDA(cudaMemsetAsync(seen.get(), 0, 2 * words * sizeof(uint32_t), s));
     residues(J, dev(), s);
     collide_and_cover(J, dev(), seen.get(), bm_off.get(), words, umask.get(), cover.get(), s);
-    int hc[2];
-    MR1L_CUDA(cudaMemcpyAsync(hc, cover.get(), sizeof(hc), cudaMemcpyDeviceToHost, s));
+    int hc_local[kCoverInts];
+    int* hc = cover_host ? cover_host : hc_local;
+    MR1L_CUDA(cudaMemcpyAsync(hc, cover.get(), kCoverInts * sizeof(int), cudaMemcpyDeviceToHost, s));
     MR1L_CUDA(cudaStreamSynchronize(s));
     Lneed = hc[0];
     n_uncovered = hc[1];
+    I_size.assign(hc + 2, hc + 2 + L);
+    first_count.assign(hc + kCoverFirst, hc + kCoverFirst + L);
   }
 
   // Chirp and filter tables of lattices 0..Luse-1; filter spectra found in
@@ -414,8 +467,8 @@ struct LatticeWork {
       sub_M.reserve(nm);
       sub_off.reserve(nm);
       sub_Bh.reserve((size_t)nm * P);
-      MR1L_CUDA(cudaMemcpyAsync(sub_M.get(), sub_Mh.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
-      MR1L_CUDA(cudaMemcpyAsync(sub_off.get(), sub_offh.data(), nm * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      stage_h2d(stage, sub_M.get(), sub_Mh.data(), nm * sizeof(int), s);
+      stage_h2d(stage, sub_off.get(), sub_offh.data(), nm * sizeof(int64_t), s);
       BlueGeom gs = geom;
       gs.L = nm;
       gs.M = sub_M.get();
@@ -429,6 +482,42 @@ struct LatticeWork {
     for (int l : miss) cache->put(Mh[l], P, Bh.get() + (size_t)l * P, s);
   }
 };
+
+// Step 2b of Algorithm 3: Algorithm 1 on J with the prime sizes `primes`,
+// repeated up to b times until condition (2.1) holds.  The GPU evaluates all
+// lattices of a search at once; with `redraw` (the rule of the remark after
+// Algorithm 1) a lattice that covers no candidate the earlier ones leave
+// uncovered has its z drawn again (at most kRedrawCap times) and the search is
+// evaluated again: lattices before it are unchanged, so the kept lattices are
+// those of the one-lattice-at-a-time rule.  Returns the searches used; lw
+// holds the last one.
+constexpr int kRedrawCap = 64;
+static int search_lattices(LatticeWork& lw, const CandSet& J, const std::vector<int>& primes, uint64_t seed, int t,
+                           int b, bool redraw, cudaStream_t s, Staging* stage) {
+  std::vector<int64_t> zs;
+  int attempts = 0;
+  for (int a = 0; a < b; ++a) {
+    std::vector<int> rd(primes.size(), 0);
+    for (;;) {
+      draw_z(seed, t, a, primes, zs, &rd);
+      lw.load(J, primes, zs, t, s);
+      if (stage) stage_reset(stage);  // load() synchronised the stream
+      if (!redraw) break;
+      const int limit = lw.n_uncovered == 0 ? lw.Lneed : (int)primes.size();
+      int idle = -1;
+      for (int l = 0; l < limit; ++l)
+        if (lw.first_count[l] == 0 && rd[l] < kRedrawCap) {
+          idle = l;
+          break;
+        }
+      if (idle < 0) break;
+      ++rd[idle];
+    }
+    attempts = a + 1;
+    if (lw.n_uncovered == 0) break;
+  }
+  return attempts;
+}
 
 // Validation shared by the plan constructors.
 static void validate_set(const int32_t* I, int64_t nI, int t) {
@@ -490,6 +579,24 @@ extern "C" int mr1l_last_error(char* buf, size_t len) {
 
 extern "C" int mr1l_version(void) { return 100; }
 
+extern "C" int mr1l_pool_stats(int device, int64_t* outstanding, int64_t* cached, int64_t* mallocs) {
+  return guarded([&] {
+    MR1L_REQUIRE(device >= 0, "device must be >= 0");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = pools().find(device);
+    if (outstanding) *outstanding = it == pools().end() ? 0 : (int64_t)it->second.outstanding;
+    if (cached) *cached = it == pools().end() ? 0 : (int64_t)it->second.cached;
+    if (mallocs) *mallocs = it == pools().end() ? 0 : it->second.mallocs;
+  });
+}
+
+extern "C" int mr1l_inject_alloc_failure(int64_t after) {
+  return guarded([&] {
+    MR1L_REQUIRE(after >= -1, "after must be >= -1");
+    g_fail_after.store(after);
+  });
+}
+
 extern "C" int mr1l_plan(const int32_t* I, int64_t nI, int t, int L, const int64_t* M, const int64_t* z, int flags,
                          void* stream, mr1l_plan_t** out) {
   return guarded([&] {
@@ -550,20 +657,14 @@ extern "C" int mr1l_plan_search(const int32_t* I, int64_t nI, int t, double c, d
     MR1L_REQUIRE(Lmax >= 1 && Lmax <= 64, "Lmax out of range");
     HostRows rows{I, t, nI, nullptr, 1};
     std::vector<int> primes = prime_set(rows, lam, Lmax);
-    std::vector<int64_t> zs;
-    for (int a = 0; a < b; ++a) {
-      draw_z(seed, t, a, primes, zs);
-      p->lw.load(p->cand(), primes, zs, t, s);
-      p->attempts = a + 1;
-      if (p->lw.n_uncovered == 0) break;
-    }
+    p->attempts = search_lattices(p->lw, p->cand(), primes, seed, t, b, (flags & MR1L_REDRAW) != 0, s, nullptr);
     int Luse = p->lw.n_uncovered == 0 ? p->lw.Lneed : Lmax;
     if (p->lw.n_uncovered && (flags & MR1L_STRICT))
       throw Error(MR1L_E_NOT_RECONSTRUCTING, "no reconstructing lattice after b searches");
     if (Luse < Lmax) {
       // drop the lattices beyond the first full coverage (Algorithm 1 stops there)
       std::vector<int> Ms(primes.begin(), primes.begin() + Luse);
-      std::vector<int64_t> z2(zs.begin(), zs.begin() + (size_t)Luse * t);
+      std::vector<int64_t> z2(p->lw.zh.begin(), p->lw.zh.begin() + (size_t)Luse * t);
       p->lw.load(p->cand(), Ms, z2, t, s);
     }
     plan_finish(p.get(), p->lw.L, s);
@@ -620,7 +721,7 @@ static void reconstruct_impl(mr1l_plan_t* plan, const void* y, int nrhs, void* c
   io.work = plan->work.get();
   blue_run(lw.geom, io, kModeRecon, nrhs, s);
   gather(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, plan->C.get(), sumM, nrhs, (cplx*)c, plan->nI,
-         nullptr, nullptr, s);
+         nullptr, nullptr, lw.pairs(), s);
 }
 
 static void evaluate_impl(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode, cudaStream_t s) {
@@ -636,7 +737,7 @@ static void evaluate_impl(mr1l_plan_t* plan, const void* c, int nrhs, void* y, i
   plan->work.reserve((size_t)nrhs * lw.Luse * lw.geom.P);
   MR1L_CUDA(cudaMemsetAsync(plan->bins.get(), 0, (size_t)nrhs * sumM * sizeof(cplx), s));
   scatter(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, (const cplx*)c, plan->nI, nrhs,
-          mode == MR1L_ADJOINT, plan->bins.get(), sumM, s);
+          mode == MR1L_ADJOINT, plan->bins.get(), sumM, lw.pairs(), s);
   BlueIO io{};
   io.in = plan->bins.get();
   io.in_stride = sumM;
@@ -765,6 +866,96 @@ static void bspline_tables(const sfft_sampler& S, int d, BsplineDev& B) {
   }
 }
 
+// Pinned host memory for the small copies of a solve.  A copy from pageable
+// host memory may wait for the stream (the driver stages it) and a copy to
+// pageable memory always does; from and to pinned memory both stay
+// asynchronous.  Released blocks are kept per process (at most 64 MiB) since
+// cudaHostAlloc is slow.
+namespace {
+std::mutex g_pinned_mu;
+std::multimap<size_t, void*>& pinned_free() {
+  static auto* m = new std::multimap<size_t, void*>();
+  return *m;
+}
+size_t g_pinned_cached = 0;
+constexpr size_t kPinnedCacheBytes = size_t(64) << 20;
+}  // namespace
+
+struct PinnedBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  PinnedBuf() = default;
+  PinnedBuf(const PinnedBuf&) = delete;
+  PinnedBuf& operator=(const PinnedBuf&) = delete;
+  ~PinnedBuf() { release(); }
+  void release() {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    if (g_pinned_cached + n <= kPinnedCacheBytes) {
+      pinned_free().emplace(n, p);
+      g_pinned_cached += n;
+    } else {
+      cudaFreeHost(p);
+    }
+    p = nullptr;
+    n = 0;
+  }
+  void* reserve(size_t bytes) {
+    if (bytes <= n && p) return p;
+    release();
+    const size_t want = std::max<size_t>(size_t(1) << 16, (bytes + 4095) / 4096 * 4096);
+    {
+      std::lock_guard<std::mutex> lk(g_pinned_mu);
+      auto it = pinned_free().lower_bound(want);
+      if (it != pinned_free().end() && it->first <= 4 * want) {
+        p = it->second;
+        n = it->first;
+        g_pinned_cached -= n;
+        pinned_free().erase(it);
+        return p;
+      }
+    }
+    MR1L_CUDA(cudaHostAlloc(&p, want, cudaHostAllocDefault));
+    n = want;
+    return p;
+  }
+};
+
+// Host-to-device staging through a pinned buffer: put() copies the source
+// into the buffer and queues the device copy from there.  The buffer is
+// reused only after the stream has been synchronised (reset()); when it is
+// full, put() synchronises first.
+struct Staging {
+  PinnedBuf buf;
+  size_t used = 0;
+  cudaStream_t s = nullptr;
+  void h2d(void* dst, const void* src, size_t bytes) {
+    if (!bytes) return;
+    const size_t need = (bytes + 255) / 256 * 256;
+    if (used + need > buf.n) {
+      if (used) {
+        MR1L_CUDA(cudaStreamSynchronize(s));
+        used = 0;
+      }
+      if (need > buf.n) buf.reserve(std::max(need, size_t(1) << 20));
+    }
+    char* pin = (char*)buf.p + used;
+    used += need;
+    std::memcpy(pin, src, bytes);
+    MR1L_CUDA(cudaMemcpyAsync(dst, pin, bytes, cudaMemcpyHostToDevice, s));
+  }
+  void reset() { used = 0; }
+};
+
+static void stage_reset(Staging* st) { st->reset(); }
+
+static void stage_h2d(Staging* st, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (st)
+    st->h2d(dst, src, bytes);
+  else if (bytes)
+    MR1L_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+}
+
 struct SfftRun {
   sfft_params P;
   sfft_sampler S;
@@ -773,6 +964,9 @@ struct SfftRun {
   double theta2;
   int rel;
   sfft_stats stats{};
+  Staging stage;
+  PinnedBuf pin_out;    // device-to-host results (selection flags, counts)
+  PinnedBuf cover_pin;  // coverage result of Algorithm 1
   // planted signal on the device (copied, or the caller's device arrays)
   DevBuf<int32_t> freqs_buf;
   DevBuf<cplx> coeffs_buf;
@@ -782,22 +976,24 @@ struct SfftRun {
   bool bspline = false;
   BsplineDev bs_host;
   DevBuf<BsplineDev> bs_dev;
-  // candidate prefix (device + host mirror) and last list
+  // candidate prefix I^(1..t-1) (device rows [np][tp]) and last list I^(t);
+  // the host reads the prefix rows back only when it needs them
   DevBuf<int32_t> pre, pre_next, last;
   std::vector<int32_t> pre_h;
   int64_t np = 0;
   int tp = 0;
+  // I^(t) of every increment from the 1-D detections (steps 1 and 2a)
+  std::vector<std::vector<int32_t>> lines;
   LatticeWork lw;
   std::unique_ptr<FilterCache> filter_cache{FilterCache::enabled() ? new FilterCache : nullptr};
-  DevBuf<double> anchors;
-  DevBuf<cplx> y, C, bins, work, pvals, coef_out;
+  DevBuf<double> anchors, line_anchors;
+  DevBuf<cplx> y, C, bins, work, pvals, coef_out, planted_w;
   DevBuf<uint64_t> keys, keymax;
   DevBuf<SelectState> sel;
   DevBuf<uint8_t> flags, line_sel;
   DevBuf<int64_t> counts;
   DevBuf<cplx> line_y, line_bins;
   std::vector<cudaEvent_t> ev;
-  std::vector<double> final_coeffs;
   // measurement noise: drawn on a side stream (its arithmetic runs on the FP32
   // pipes) while the main stream runs the sampler's inverse transform on the
   // FP64 pipe, then added to the samples by the reconstruct pass as it loads
@@ -813,6 +1009,11 @@ struct SfftRun {
     if (side) cudaStreamDestroy(side);
   }
 
+  void sync() {
+    MR1L_CUDA(cudaStreamSynchronize(s));
+    stage.reset();
+  }
+
   void noise_setup() {
     if (side) return;
     MR1L_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
@@ -823,8 +1024,8 @@ struct SfftRun {
   void ev_record() {
     cudaEvent_t e;
     MR1L_CUDA(cudaEventCreate(&e));
-    MR1L_CUDA(cudaEventRecord(e, s));
     ev.push_back(e);
+    MR1L_CUDA(cudaEventRecord(e, s));
   }
 
   std::vector<double> anchor_rows(uint32_t purpose, int t, int rep0, int count) {
@@ -837,58 +1038,76 @@ struct SfftRun {
     return a;
   }
 
-  // Steps 1 / 2a: I^(t) from r random lines.
-  std::vector<int32_t> detect(int t) {
-    const int r = P.r;
-    std::vector<double> a = anchor_rows(kAnchorLine, t, 0, r);
-    anchors.reserve(a.size());
-    MR1L_CUDA(cudaMemcpyAsync(anchors.get(), a.data(), a.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    line_y.reserve((size_t)r * K);
+  // Steps 1 and 2a for every increment: I^(t) from r random lines through
+  // the t-th coordinate.  They do not depend on the lattice steps, so all d
+  // are queued at once (in chunks of increments whose line samples fit
+  // kLineChunkBytes, each increment in its own slot so that a user sampler
+  // that writes synchronously cannot overwrite lines still being read) and
+  // read back with one synchronisation per chunk.
+  void detect_all() {
+    const int r = P.r, d = P.d;
+    constexpr size_t kLineChunkBytes = size_t(256) << 20;
+    const size_t per_t = (size_t)r * K * sizeof(cplx);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(d, kLineChunkBytes / per_t));
+    line_y.reserve((size_t)chunk * r * K);
     line_bins.reserve((size_t)r * K);
-    line_sel.reserve(K);
-    ev_record();
-    if (S.fn) {
-      for (int i = 0; i < r; ++i) {
-        sfft_request q{};
-        q.kind = SFFT_REQ_LINE;
-        q.t = t;
-        q.rep = i;
-        q.d = P.d;
-        q.anchors = a.data() + (size_t)i * P.d;
-        q.K = K;
-        int rc = S.fn(S.user, &q, line_y.get() + (size_t)i * K, s);
-        if (rc != 0) throw Error(MR1L_E_SAMPLER, "sampler callback failed (line request)");
+    line_anchors.reserve((size_t)chunk * r * d);
+    line_sel.reserve((size_t)d * K);
+    uint8_t* hsel = (uint8_t*)pin_out.reserve((size_t)d * K);
+    MR1L_CUDA(cudaMemsetAsync(line_sel.get(), 0, (size_t)d * K, s));
+    lines.assign(d + 1, {});
+    for (int t0 = 1; t0 <= d; t0 += chunk) {
+      const int t1 = std::min(d, t0 + chunk - 1);
+      for (int t = t0; t <= t1; ++t) {
+        const int slot = t - t0;
+        cplx* ly = line_y.get() + (size_t)slot * r * K;
+        double* la = line_anchors.get() + (size_t)slot * r * d;
+        std::vector<double> a = anchor_rows(kAnchorLine, t, 0, r);
+        stage.h2d(la, a.data(), a.size() * sizeof(double));
+        ev_record();
+        if (S.fn) {
+          for (int i = 0; i < r; ++i) {
+            sfft_request q{};
+            q.kind = SFFT_REQ_LINE;
+            q.t = t;
+            q.rep = i;
+            q.d = d;
+            q.anchors = a.data() + (size_t)i * d;
+            q.K = K;
+            int rc = S.fn(S.user, &q, ly + (size_t)i * K, s);
+            if (rc != 0) throw Error(MR1L_E_SAMPLER, "sampler callback failed (line request, t = " + std::to_string(t) + ")");
+          }
+        } else if (bspline) {
+          bspline_lines(bs_dev.get(), t, K, la, r, ly, s);
+        } else {
+          planted_lines(freqs_ptr, coeffs_ptr, S.s, d, t, K, la, r, S.sigma / std::sqrt(2.0), S.noise_seed, 0,
+                        line_bins.get(), ly, s);
+        }
+        ev_record();
+        detect_lines(ly, r, P.N, P.s_local, theta2, rel, line_sel.get() + (size_t)(t - 1) * K, s);
       }
-    } else if (bspline) {
-      bspline_lines(bs_dev.get(), t, K, anchors.get(), r, line_y.get(), s);
-    } else {
-      planted_lines(freqs_ptr, coeffs_ptr, S.s, P.d, t, K, anchors.get(), r, S.sigma / std::sqrt(2.0),
-                    S.noise_seed, 0, line_bins.get(), line_y.get(), s);
+      MR1L_CUDA(cudaMemcpyAsync(hsel + (size_t)(t0 - 1) * K, line_sel.get() + (size_t)(t0 - 1) * K,
+                                (size_t)(t1 - t0 + 1) * K, cudaMemcpyDeviceToHost, s));
+      sync();
+      for (int t = t0; t <= t1; ++t)
+        for (int a2 = 0; a2 < K; ++a2)
+          if (hsel[(size_t)(t - 1) * K + a2]) lines[t].push_back(a2 - P.N);
     }
-    ev_record();
-    MR1L_CUDA(cudaMemsetAsync(line_sel.get(), 0, K, s));
-    detect_lines(line_y.get(), r, P.N, P.s_local, theta2, rel, line_sel.get(), s);
-    std::vector<uint8_t> h(K);
-    MR1L_CUDA(cudaMemcpyAsync(h.data(), line_sel.get(), K, cudaMemcpyDeviceToHost, s));
-    MR1L_CUDA(cudaStreamSynchronize(s));
-    std::vector<int32_t> out;
-    for (int a2 = 0; a2 < K; ++a2)
-      if (h[a2]) out.push_back(a2 - P.N);
-    return out;
   }
 
   // One group of repetitions [rep0, rep0 + nrep): sample, reconstruct, select.
-  void passes(const CandSet& J, int t, int rep0, int nrep, int64_t cap, int last_pass) {
+  void passes(const CandSet& J, int t, int rep0, int nrep, int64_t cap) {
     const int64_t n = J.n();
     const int64_t sumM = lw.sumM;
     std::vector<double> a = anchor_rows(kAnchorLattice, t, rep0, nrep);
     anchors.reserve(a.size());
-    MR1L_CUDA(cudaMemcpyAsync(anchors.get(), a.data(), a.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    stage.h2d(anchors.get(), a.data(), a.size() * sizeof(double));
     y.reserve((size_t)nrep * sumM);
     C.reserve((size_t)nrep * sumM);
     work.reserve((size_t)nrep * lw.Luse * lw.geom.P);
     ev_record();
     if (S.fn) {
+      std::vector<int64_t> Ml(lw.Mh.begin(), lw.Mh.begin() + lw.Luse);
       for (int i = 0; i < nrep; ++i) {
         sfft_request q{};
         q.kind = SFFT_REQ_LATTICE;
@@ -897,12 +1116,12 @@ struct SfftRun {
         q.d = P.d;
         q.anchors = a.data() + (size_t)i * P.d;
         q.L = lw.Luse;
-        std::vector<int64_t> Ml(lw.Mh.begin(), lw.Mh.begin() + lw.Luse);
         q.M = Ml.data();
         q.z = lw.zh.data();
         q.sum_M = sumM;
         int rc = S.fn(S.user, &q, y.get() + (size_t)i * sumM, s);
-        if (rc != 0) throw Error(MR1L_E_SAMPLER, "sampler callback failed (lattice request)");
+        if (rc != 0)
+          throw Error(MR1L_E_SAMPLER, "sampler callback failed (lattice request, t = " + std::to_string(t) + ")");
       }
     } else if (bspline) {
       int maxM = 0;
@@ -931,8 +1150,9 @@ struct SfftRun {
       }
       bins.reserve((size_t)nrep * sumM);
       MR1L_CUDA(cudaMemsetAsync(bins.get(), 0, (size_t)nrep * sumM * sizeof(cplx), s));
+      planted_w.reserve(std::max<int64_t>((int64_t)nrep * S.s, 1));
       planted_lattice_bins(freqs_ptr, coeffs_ptr, S.s, P.d, t, anchors.get(), nrep, lw.dev(), lw.Luse, lw.geom,
-                           bins.get(), sumM, s);
+                           bins.get(), sumM, planted_w.get(), s);
       BlueIO io{};
       io.in = bins.get();
       io.in_stride = sumM;
@@ -946,7 +1166,7 @@ struct SfftRun {
     BlueIO io{};
     io.in = y.get();
     io.in_stride = sumM;
-    io.add_in = (!S.fn && S.sigma > 0) ? noise.get() : nullptr;
+    io.add_in = (!S.fn && !bspline && S.sigma > 0) ? noise.get() : nullptr;
     io.out = C.get();
     io.out_stride = sumM;
     io.work = work.get();
@@ -957,23 +1177,35 @@ struct SfftRun {
     sel.reserve(nrep);
     MR1L_CUDA(cudaMemsetAsync(keymax.get(), 0, nrep * sizeof(uint64_t), s));
     gather(J, lw.dev(), lw.Luse, lw.umask.get(), lw.geom, C.get(), sumM, nrep, pvals.get(), n, keys.get(),
-           keymax.get(), s);
+           keymax.get(), lw.pairs(), s);
     select_topk(keys.get(), n, nrep, keymax.get(), theta2, rel, cap, sel.get(), flags.get(), s);
-    (void)last_pass;
+  }
+
+  // The prefix rows on the host (read back from the device when needed).
+  const int32_t* prefix_host() {
+    if ((int64_t)pre_h.size() != np * tp) {
+      pre_h.resize(np * tp);
+      if (np) MR1L_CUDA(cudaMemcpyAsync(pre_h.data(), pre.get(), np * tp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      sync();
+    }
+    return pre_h.data();
   }
 
   void run(sfft_result* res) {
     auto t0 = std::chrono::steady_clock::now();
     const int d = P.d;
     K = 2 * P.N + 1;
+    stage.s = s;
     lw.df = P.fft_arith ? 1 : 0;
+    lw.stage = &stage;
+    lw.cover_host = (int*)cover_pin.reserve(kCoverInts * sizeof(int));
     theta2 = P.theta * P.theta;
     rel = P.theta_mode == SFFT_THETA_REL;
     bspline = !S.fn && S.kind == SFFT_SAMPLER_BSPLINE;
     if (bspline) {
       bspline_tables(S, d, bs_host);
       bs_dev.reserve(1);
-      MR1L_CUDA(cudaMemcpyAsync(bs_dev.get(), &bs_host, sizeof(BsplineDev), cudaMemcpyHostToDevice, s));
+      stage.h2d(bs_dev.get(), &bs_host, sizeof(BsplineDev));
     } else if (!S.fn && !S.device_arrays) {
       freqs_buf.reserve(std::max<int64_t>(S.s * d, 1));
       coeffs_buf.reserve(std::max<int64_t>(S.s, 1));
@@ -987,20 +1219,31 @@ struct SfftRun {
       freqs_ptr = S.freqs;
       coeffs_ptr = (const cplx*)S.coeffs;
     }
-    // step 1
-    std::vector<int32_t> I1 = detect(1);
+    // steps 1 and 2a for all increments
+    detect_all();
+    // the component ranges of the 1-D sets bound those of every candidate set
+    // (a candidate's j-th component lies in I^(j))
+    std::vector<int64_t> range(d + 1, 0);
+    for (int t = 1; t <= d; ++t)
+      if (!lines[t].empty())
+        range[t] = *std::max_element(lines[t].begin(), lines[t].end()) -
+                   *std::min_element(lines[t].begin(), lines[t].end());
+    const std::vector<int32_t>& I1 = lines[1];
     stats.samples += (int64_t)P.r * K;
-    pre_h.assign(I1.begin(), I1.end());
     np = (int64_t)I1.size();
     tp = 1;
-    std::vector<cplx> coef_h;
+    pre.reserve(std::max<int64_t>(np, 1));
+    stage.h2d(pre.get(), I1.data(), np * sizeof(int32_t));
+    pre_h.assign(I1.begin(), I1.end());
+    int64_t range_bound = range[1];
     // step 2
     for (int t = 2; t <= d; ++t) {
-      std::vector<int32_t> It = detect(t);
+      const std::vector<int32_t>& It = lines[t];
       sfft_step_stats& st = stats.steps[stats.n_steps++];
       st.t = t;
       st.n_line = (int)It.size();
       st.samples = (int64_t)P.r * K;
+      range_bound = std::max(range_bound, range[t]);
       const int rt = t < d ? P.r : 1;
       const int64_t cap = t < d ? P.s_local : P.s;
       const int64_t n = np * (int64_t)It.size();
@@ -1013,10 +1256,8 @@ struct SfftRun {
         st.covered = 1;
         continue;
       }
-      pre.reserve(np * tp);
-      MR1L_CUDA(cudaMemcpyAsync(pre.get(), pre_h.data(), np * tp * sizeof(int32_t), cudaMemcpyHostToDevice, s));
       last.reserve(It.size());
-      MR1L_CUDA(cudaMemcpyAsync(last.get(), It.data(), It.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      stage.h2d(last.get(), It.data(), It.size() * sizeof(int32_t));
       CandSet J;
       J.tp = tp;
       J.t = t;
@@ -1029,16 +1270,13 @@ struct SfftRun {
       double lam;
       lmax_lambda(n, 2.0, 0.5, Lmax, lam);
       MR1L_REQUIRE(Lmax >= 1 && Lmax <= 64, "Lmax out of range");
-      HostRows rows{pre_h.data(), tp, np, It.data(), (int64_t)It.size()};
+      // primes above the bound on the component ranges are in P^J without a
+      // look at the rows; smaller ones are checked on the host rows
+      HostRows rows{nullptr, tp, np, It.data(), (int64_t)It.size()};
+      if ((int64_t)std::floor(lam) + 1 <= range_bound) rows.pre = prefix_host();
+      rows.range_bound = range_bound;
       std::vector<int> primes = prime_set(rows, lam, Lmax);
-      std::vector<int64_t> zs;
-      int attempts = 0;
-      for (int a = 0; a < P.b; ++a) {
-        draw_z(P.seed, t, a, primes, zs);
-        lw.load(J, primes, zs, t, s);
-        attempts = a + 1;
-        if (lw.n_uncovered == 0) break;
-      }
+      const int attempts = search_lattices(lw, J, primes, P.seed, t, P.b, P.redraw != 0, s, &stage);
       const int covered = lw.n_uncovered == 0;
       const int Luse = covered ? lw.Lneed : Lmax;
       lw.tables(Luse, s, filter_cache ? filter_cache.get() : nullptr);
@@ -1050,32 +1288,38 @@ struct SfftRun {
       MR1L_CUDA(cudaMemsetAsync(flags.get(), 0, n, s));
       // steps 2c-2e
       if (P.batch_reps) {
-        passes(J, t, 0, rt, cap, 1);
+        passes(J, t, 0, rt, cap);
       } else {
-        for (int i = 0; i < rt; ++i) passes(J, t, i, 1, cap, i == rt - 1);
+        for (int i = 0; i < rt; ++i) passes(J, t, i, 1, cap);
       }
       st.samples += (int64_t)rt * (1 - Luse + lw.sumM);
       stats.samples += st.samples;
-      // compaction: next prefix I^(1..t) (and the coefficients at t = d)
+      // compaction: next prefix I^(1..t) on the device (and the coefficients
+      // at t = d); only the count comes back
       pre_next.reserve(n * t);
       counts.reserve(cdiv(n, 1024) + 1);
       if (t == d) coef_out.reserve(n);
       int64_t cnt = compact(J, flags.get(), pre_next.get(), t == d ? pvals.get() : nullptr,
-                            t == d ? coef_out.get() : nullptr, counts.get(), (int64_t)counts.n, s);
+                            t == d ? coef_out.get() : nullptr, counts.get(), (int64_t)counts.n,
+                            (int64_t*)pin_out.reserve(sizeof(int64_t)), s);
+      stage.reset();  // compact() synchronised the stream
+      std::swap(pre.p, pre_next.p);
+      std::swap(pre.n, pre_next.n);
+      std::swap(pre.block, pre_next.block);
+      std::swap(pre.device, pre_next.device);
       np = cnt;
       tp = t;
-      pre_h.resize(np * tp);
-      if (np)
-        MR1L_CUDA(cudaMemcpyAsync(pre_h.data(), pre_next.get(), np * tp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      if (t == d) {
-        coef_h.resize(np);
-        if (np) MR1L_CUDA(cudaMemcpyAsync(coef_h.data(), coef_out.get(), np * sizeof(cplx), cudaMemcpyDeviceToHost, s));
-      }
-      MR1L_CUDA(cudaStreamSynchronize(s));
+      pre_h.clear();
       st.n_detected = np;
       if (P.t_stop && t == P.t_stop) break;
     }
-    MR1L_CUDA(cudaStreamSynchronize(s));
+    std::vector<cplx> coef_h;
+    if (tp == d && np) {
+      coef_h.resize(np);
+      MR1L_CUDA(cudaMemcpyAsync(coef_h.data(), coef_out.get(), np * sizeof(cplx), cudaMemcpyDeviceToHost, s));
+    }
+    const int32_t* rows_h = prefix_host();
+    sync();
     double samp = 0.0;
     for (size_t i = 0; i + 1 < ev.size(); i += 2) {
       float ms = 0.f;
@@ -1091,7 +1335,7 @@ struct SfftRun {
     res->coeffs = (double*)std::calloc(std::max<int64_t>(np, 1) * 2, sizeof(double));
     if (!res->freqs || !res->coeffs) throw std::bad_alloc();
     if (np) {
-      std::memcpy(res->freqs, pre_h.data(), np * dout * sizeof(int32_t));
+      std::memcpy(res->freqs, rows_h, np * dout * sizeof(int32_t));
       if ((int64_t)coef_h.size() == np) std::memcpy(res->coeffs, coef_h.data(), np * sizeof(cplx));
     }
     res->stats = stats;
@@ -1112,6 +1356,7 @@ static void validate_sfft(const sfft_params* params, const sfft_sampler* sampler
   MR1L_REQUIRE(P.theta_mode == SFFT_THETA_ABS || P.theta_mode == SFFT_THETA_REL, "bad theta_mode");
   MR1L_REQUIRE(P.t_stop == 0 || (P.t_stop >= 2 && P.t_stop <= P.d), "t_stop must be 0 or in [2, d]");
   MR1L_REQUIRE(P.zero_anchors == 0 || P.zero_anchors == 1, "zero_anchors must be 0 or 1");
+  MR1L_REQUIRE(P.redraw == 0 || P.redraw == 1, "redraw must be 0 or 1");
   MR1L_REQUIRE(P.fft_arith == 0 || P.fft_arith == 1, "fft_arith must be 0 (FP64) or 1 (double-float)");
   if (!sampler->fn && sampler->kind == SFFT_SAMPLER_BSPLINE) {
     const sfft_sampler& S = *sampler;
@@ -1191,6 +1436,29 @@ extern "C" int sfft_dimincr_batch(const sfft_params* params, const sfft_sampler*
     for (auto& th : pool) th.join();
     for (int i = 0; i < count; ++i)
       if (status[i] != MR1L_OK) throw Error(status[i], "problem " + std::to_string(i) + " failed: " + why[i]);
+  });
+}
+
+extern "C" int sfft_select(const void* p, int64_t n, int nrhs, const uint8_t* eligible, int64_t cap, double theta,
+                           int theta_mode, uint8_t* flags, void* stream) {
+  return guarded([&] {
+    MR1L_REQUIRE(n >= 0 && nrhs >= 0 && nrhs <= 65535, "need n >= 0 and 0 <= nrhs <= 65535");
+    MR1L_REQUIRE(cap >= 0, "cap must be >= 0");
+    MR1L_REQUIRE(theta >= 0.0 && std::isfinite(theta), "theta must be finite and >= 0");
+    MR1L_REQUIRE(theta_mode == SFFT_THETA_ABS || theta_mode == SFFT_THETA_REL, "bad theta_mode");
+    if (n == 0 || nrhs == 0 || cap == 0) return;
+    MR1L_REQUIRE(p != nullptr && flags != nullptr, "null array");
+    MR1L_REQUIRE(((uintptr_t)p & 15) == 0, "p must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf<uint64_t> keys, keymax;
+    DevBuf<SelectState> st;
+    keys.reserve((size_t)nrhs * n);
+    keymax.reserve(nrhs);
+    st.reserve(nrhs);
+    value_keys((const cplx*)p, n, nrhs, eligible, keys.get(), keymax.get(), s);
+    select_topk(keys.get(), n, nrhs, keymax.get(), theta * theta, theta_mode == SFFT_THETA_REL, cap, st.get(), flags,
+                s);
+    // the scratch goes back to the block cache, which waits for the device
   });
 }
 
@@ -1281,7 +1549,7 @@ extern "C" int mr1l_reconstruct_noalloc(mr1l_plan_t* plan, const void* y, int nr
     io.no_tune = 1;  // tiling trials would synchronise and create events
     blue_run(lw.geom, io, kModeRecon, nrhs, s);
     gather(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, Cbuf, sumM, nrhs, (cplx*)c, plan->nI,
-           nullptr, nullptr, s);
+           nullptr, nullptr, lw.pairs(), s);
   });
 }
 

@@ -53,20 +53,23 @@ void set_last_error(int code, const std::string& msg);
 // synchronises the device first, as the cudaFree it replaces does, so a cached
 // block is never handed out while queued work may still use it.
 // ---------------------------------------------------------------------------
-void* dev_alloc(size_t bytes, size_t* block_bytes);
-void dev_free(void* p, size_t block_bytes);
+// A block belongs to the device that was current when it was allocated;
+// dev_free returns it to that device's cache whatever device is current then.
+void* dev_alloc(size_t bytes, size_t* block_bytes, int* device);
+void dev_free(void* p, size_t block_bytes, int device);
 
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
   size_t block = 0;  // bytes of the block behind p
+  int device = 0;    // device that owns the block
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) dev_free(p, block);
+    if (p) dev_free(p, block, device);
     p = nullptr;
     n = 0;
     block = 0;
@@ -76,7 +79,7 @@ struct DevBuf {
     if (count <= n && p) return p;
     release();
     size_t bytes = (count ? count : 1) * sizeof(T);
-    p = (T*)dev_alloc(bytes, &block);
+    p = (T*)dev_alloc(bytes, &block, &device);
     n = count;
     return p;
   }

@@ -52,10 +52,13 @@ __global__ void last_res_kernel(CandSet J, LatticeDev lat) {
 }
 
 void residues(const CandSet& J, const LatticeDev& lat, cudaStream_t s) {
+  // algorithmic bytes: the rows read once, the factors written
   if (J.np > 0) {
-    MR1L_LAUNCH("pre_res_kernel", s, 0, 0, pre_res_kernel<<<dim3(cdiv(J.np, 256), lat.L), 256, 0, s>>>(J, lat));
+    MR1L_LAUNCH("pre_res_kernel", s, 0, 4.0 * J.np * (J.tp + lat.L),
+                pre_res_kernel<<<dim3(cdiv(J.np, 256), lat.L), 256, 0, s>>>(J, lat));
   }
-  MR1L_LAUNCH("last_res_kernel", s, 0, 0, last_res_kernel<<<dim3(cdiv(J.nq, 256), lat.L), 256, 0, s>>>(J, lat));
+  MR1L_LAUNCH("last_res_kernel", s, 0, 4.0 * J.nq * (1 + lat.L),
+              last_res_kernel<<<dim3(cdiv(J.nq, 256), lat.L), 256, 0, s>>>(J, lat));
 }
 
 // ---------------------------------------------------------------------------
@@ -79,15 +82,17 @@ __global__ void collide_kernel(CandSet J, LatticeDev lat, uint32_t* seen1, uint3
 }
 
 // umask[c]: lattices in which c is collision-free; cover[0] = max over covered
-// c of (first covering lattice + 1); cover[1] = uncovered count.
+// c of (first covering lattice + 1); cover[1] = uncovered count; cover[2 + l]
+// = |I_l| (the number of candidates collision-free in lattice l); cover[66 +
+// l] = the number of candidates whose first collision-free lattice is l.
 __global__ void cover_kernel(CandSet J, LatticeDev lat, const uint32_t* seen2, const int64_t* bm_off,
                              uint64_t* umask, int* cover) {
   const int64_t n = J.np * J.nq;
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned need = 0, unc = 0;
+  uint64_t m = 0;
   if (c < n) {
     int64_t p = c / J.nq, q = c - p * J.nq;
-    uint64_t m = 0;
     for (int l = 0; l < lat.L; ++l) {
       uint32_t r = residue_of(lat, J.np, J.nq, l, p, q, (uint32_t)lat.M[l]);
       if (!(seen2[bm_off[l] + (r >> 5)] & (1u << (r & 31)))) m |= (uint64_t)1 << l;
@@ -102,16 +107,33 @@ __global__ void cover_kernel(CandSet J, LatticeDev lat, const uint32_t* seen2, c
     if (need) atomicMax(cover, (int)need);
     if (unc) atomicAdd(cover + 1, (int)unc);
   }
+  // per-lattice sizes |I_l| and first-covering counts: one ballot per
+  // lattice and warp
+  const int first = m ? __ffsll((long long)m) - 1 : -1;
+  for (int l = 0; l < lat.L; ++l) {
+    const unsigned b = __ballot_sync(0xffffffffu, (m >> l) & 1);
+    const unsigned f = __ballot_sync(0xffffffffu, first == l);
+    if ((threadIdx.x & 31) == 0) {
+      if (b) atomicAdd(cover + 2 + l, __popc(b));
+      if (f) atomicAdd(cover + 2 + 64 + l, __popc(f));
+    }
+  }
 }
 
 void collide_and_cover(const CandSet& J, const LatticeDev& lat, uint32_t* seen, const int64_t* bm_off,
                        int64_t words, uint64_t* umask, int* cover, cudaStream_t s) {
   const int64_t n = J.n();
-  MR1L_CUDA(cudaMemsetAsync(cover, 0, 2 * sizeof(int), s));
+  MR1L_CUDA(cudaMemsetAsync(cover, 0, (2 + 128) * sizeof(int), s));
   if (n == 0) return;
   int blocks = (int)std::min<int64_t>(cdiv(n, 256), 4096);
-  MR1L_LAUNCH("collide_kernel", s, 0, 0, collide_kernel<<<dim3(blocks, lat.L), 256, 0, s>>>(J, lat, seen, seen + words, bm_off));
-  MR1L_LAUNCH("cover_kernel", s, 0, 0, cover_kernel<<<cdiv(n, 256), 256, 0, s>>>(J, lat, seen + words, bm_off, umask, cover));
+  // algorithmic bytes: the residue factors read once, the two bitmaps
+  // written once (collide); the factors and the second bitmap read, the masks
+  // written (cover)
+  const double factors = 4.0 * lat.L * (double)(J.np + J.nq), bitmaps = 4.0 * 2 * words;
+  MR1L_LAUNCH("collide_kernel", s, 0, factors + bitmaps,
+              collide_kernel<<<dim3(blocks, lat.L), 256, 0, s>>>(J, lat, seen, seen + words, bm_off));
+  MR1L_LAUNCH("cover_kernel", s, 0, factors + bitmaps / 2 + 8.0 * n,
+              cover_kernel<<<cdiv(n, 256), 256, 0, s>>>(J, lat, seen + words, bm_off, umask, cover));
 }
 
 // ---------------------------------------------------------------------------
@@ -119,52 +141,97 @@ void collide_and_cover(const CandSet& J, const LatticeDev& lat, uint32_t* seen, 
 // keys: bits(|p~|^2) + 1 for covered candidates (order-preserving for
 // non-negative doubles), 0 for uncovered ones.
 // ---------------------------------------------------------------------------
-__global__ void gather_kernel(CandSet J, LatticeDev lat, uint64_t lmask, const uint64_t* umask,
-                              const int64_t* off, const cplx* w, const cplx* C, int64_t C_stride, cplx* out,
-                              int64_t out_stride, uint64_t* keys, uint64_t* keymax) {
-  const int h = blockIdx.y;
+// One thread per candidate and group of G right-hand sides: the residue,
+// mask and chirp of each (candidate, lattice) pair are read once for the
+// whole group, and the group's samples at that residue are independent loads
+// in flight together.  Per right-hand side the lattices are summed in
+// ascending order, whatever G is, so every G gives the same bits.
+template <int kGatherRhs>
+__global__ void __launch_bounds__(256) gather_kernel(CandSet J, LatticeDev lat, uint64_t lmask, const uint64_t* umask,
+                                                     const int64_t* off, const cplx* w, const cplx* C, int64_t C_stride,
+                                                     int nrhs, cplx* out, int64_t out_stride, uint64_t* keys,
+                                                     uint64_t* keymax) {
+  const int h0 = blockIdx.y * kGatherRhs;
+  const int nh = min(kGatherRhs, nrhs - h0);
   const int64_t n = J.np * J.nq;
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  uint64_t key = 0;
+  cplx acc[kGatherRhs];
+#pragma unroll
+  for (int i = 0; i < kGatherRhs; ++i) acc[i] = cmake(0.0, 0.0);
+  int cnt = 0;
   if (c < n) {
-    int64_t p = c / J.nq, q = c - p * J.nq;
+    const int64_t p = c / J.nq, q = c - p * J.nq;
     uint64_t m = umask[c] & lmask;
-    int cnt = __popcll(m);
-    const cplx* Ch = C + h * C_stride;
-    cplx acc = cmake(0.0, 0.0);
+    cnt = __popcll(m);
+    const cplx* Ch = C + h0 * C_stride;
     while (m) {
-      int l = __ffsll((long long)m) - 1;
+      const int l = __ffsll((long long)m) - 1;
       m &= m - 1;
-      uint32_t r = residue_of(lat, J.np, J.nq, l, p, q, (uint32_t)lat.M[l]);
-      int64_t o = off[l] + r;
-      cplx v = cmul(w[o], Ch[o]);
-      acc.x += v.x;
-      acc.y += v.y;
+      const uint32_t r = residue_of(lat, J.np, J.nq, l, p, q, (uint32_t)lat.M[l]);
+      const int64_t o = off[l] + r;
+      const cplx wo = w[o];
+      cplx y[kGatherRhs];
+#pragma unroll
+      for (int i = 0; i < kGatherRhs; ++i)
+        if (i < nh) y[i] = Ch[i * C_stride + o];
+#pragma unroll
+      for (int i = 0; i < kGatherRhs; ++i)
+        if (i < nh) {
+          const cplx v = cmul(wo, y[i]);
+          acc[i].x += v.x;
+          acc[i].y += v.y;
+        }
     }
-    cplx res = cmake(0.0, 0.0);
-    if (cnt) {
-      double inv = __drcp_rn((double)cnt);
-      res = cmake(acc.x * inv, acc.y * inv);
-      double k2 = __dadd_rn(__dmul_rn(res.x, res.x), __dmul_rn(res.y, res.y));
-      key = (uint64_t)__double_as_longlong(k2) + 1;
-    }
-    out[h * out_stride + c] = res;
-    if (keys) keys[h * n + c] = key;
   }
-  if (keymax) {
-    key = warp_max_u64(key);
-    if ((threadIdx.x & 31) == 0 && key) atomicMax((unsigned long long*)(keymax + h), (unsigned long long)key);
+  const double inv = cnt ? __drcp_rn((double)cnt) : 0.0;
+#pragma unroll
+  for (int i = 0; i < kGatherRhs; ++i) {
+    if (i >= nh) break;  // uniform across the block
+    const int h = h0 + i;
+    uint64_t key = 0;
+    if (c < n) {
+      cplx res = cmake(0.0, 0.0);
+      if (cnt) {
+        res = cmake(acc[i].x * inv, acc[i].y * inv);
+        const double k2 = __dadd_rn(__dmul_rn(res.x, res.x), __dmul_rn(res.y, res.y));
+        key = (uint64_t)__double_as_longlong(k2) + 1;
+      }
+      out[h * out_stride + c] = res;
+      if (keys) keys[h * n + c] = key;
+    }
+    if (keymax) {
+      key = warp_max_u64(key);
+      if ((threadIdx.x & 31) == 0 && key) atomicMax((unsigned long long*)(keymax + h), (unsigned long long)key);
+    }
   }
 }
 
 void gather(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
             const cplx* C, int64_t C_stride, int nrhs, cplx* p, int64_t p_stride, uint64_t* keys,
-            uint64_t* keymax, cudaStream_t s) {
+            uint64_t* keymax, int64_t pairs, cudaStream_t s) {
   const int64_t n = J.n();
   if (n == 0 || nrhs == 0) return;
   uint64_t lmask = Luse >= 64 ? ~0ull : ((1ull << Luse) - 1);
-  MR1L_LAUNCH("gather_kernel", s, 0, 0, gather_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, g.w, C, C_stride, p,
-                                                          p_stride, keys, keymax));
+  // algorithmic bytes: the samples of every right-hand side at every (k, l)
+  // with k in I_l and the chirp there, the masks, the coefficients (and keys)
+  const double bytes = 16.0 * pairs * (nrhs + 1) + 8.0 * n + (double)nrhs * (keys ? 24.0 : 16.0) * n;
+  // the largest group that still leaves about 2^18 threads to hide the
+  // latency of the random reads
+  auto threads = [&](int G) { return (int64_t)cdiv(n, 256) * 256 * cdiv(nrhs, G); };
+  const int G = threads(8) >= (1 << 18) ? 8 : threads(4) >= (1 << 18) ? 4 : threads(2) >= (1 << 18) ? 2 : 1;
+#define MR1L_GATHER(GG)                                                                                         \
+  MR1L_LAUNCH("gather_kernel", s, 0, bytes,                                                                   \
+              gather_kernel<GG><<<dim3(cdiv(n, 256), cdiv(nrhs, GG)), 256, 0, s>>>(                          \
+                  J, lat, lmask, umask, g.off, g.w, C, C_stride, nrhs, p, p_stride, keys, keymax))
+  if (G == 8)
+    MR1L_GATHER(8);
+  else if (G == 4)
+    MR1L_GATHER(4);
+  else if (G == 2)
+    MR1L_GATHER(2);
+  else
+    MR1L_GATHER(1);
+#undef MR1L_GATHER
 }
 
 // ---------------------------------------------------------------------------
@@ -207,12 +274,17 @@ __global__ void scatter_kernel(CandSet J, LatticeDev lat, uint64_t lmask, const 
 
 void scatter(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
              const cplx* coef, int64_t coef_stride, int nrhs, int adjoint, cplx* bins, int64_t bins_stride,
-             cudaStream_t s) {
+             int64_t pairs, cudaStream_t s) {
   const int64_t n = J.n();
   if (n == 0 || nrhs == 0) return;
   uint64_t lmask = Luse >= 64 ? ~0ull : ((1ull << Luse) - 1);
-  MR1L_LAUNCH("scatter_kernel", s, 0, 0, scatter_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, coef, coef_stride,
-                                                           adjoint, bins, bins_stride));
+  // algorithmic bytes: the coefficients (and masks) in, one complex
+  // read-modify-write per (k, l) pair (all lattices for EVAL, k in I_l for ADJOINT)
+  const double bytes = (double)nrhs * (16.0 * n + 32.0 * (adjoint ? pairs : n * (int64_t)Luse)) +
+                       (adjoint ? 8.0 * n : 0.0);
+  MR1L_LAUNCH("scatter_kernel", s, 0, bytes,
+              scatter_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, coef, coef_stride,
+                                                                       adjoint, bins, bins_stride));
 }
 
 // ---------------------------------------------------------------------------
@@ -230,34 +302,55 @@ __device__ __forceinline__ cplx planted_weight(const int32_t* f, cplx c, const d
   return cmul(c, cmake(cs, sn));
 }
 
-// one thread per (planted frequency, lattice, right-hand side)
-__global__ void planted_lattice_kernel(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
-                                       const double* anchors, LatticeDev lat, const int64_t* off, cplx* bins,
+// The weight c_h e^{2 pi i h_(>t).x'} of a planted frequency depends on the
+// right-hand side (its anchor) but not on the lattice, and the bin
+// h_(1..t).z_l mod M_l on the lattice but not on the right-hand side: the
+// weights are computed once per (frequency, rhs), the residues once per
+// (frequency, lattice).
+__global__ void planted_weights_kernel(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
+                                       const double* anchors, cplx* wts) {
+  const int h = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= s_count) return;
+  wts[h * s_count + i] = planted_weight(freqs + i * d, coeffs[i], anchors + (int64_t)h * d, t, d, -1);
+}
+
+// one thread per (planted frequency, lattice): the bin, then one atomic add per rhs
+__global__ void planted_lattice_kernel(const int32_t* freqs, int64_t s_count, int d, int t, int nrhs,
+                                       const cplx* wts, LatticeDev lat, const int64_t* off, cplx* bins,
                                        int64_t bins_stride) {
-  const int l = blockIdx.y, h = blockIdx.z;
+  const int l = blockIdx.y;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= s_count) return;
   const int32_t* f = freqs + i * d;
-  const cplx wv = planted_weight(f, coeffs[i], anchors + (int64_t)h * d, t, d, -1);
   const int64_t M = lat.M[l];
   const int64_t* z = lat.z + (int64_t)l * lat.t;
   int64_t acc = 0;
   for (int j = 0; j < t; ++j) acc += (int64_t)f[j] * z[j];
   acc %= M;
   if (acc < 0) acc += M;
-  double* dst = (double*)(bins + h * bins_stride + off[l] + acc);
-  atomicAdd(dst, wv.x);
-  atomicAdd(dst + 1, wv.y);
+  for (int h = 0; h < nrhs; ++h) {
+    const cplx wv = wts[h * s_count + i];
+    double* dst = (double*)(bins + h * bins_stride + off[l] + acc);
+    atomicAdd(dst, wv.x);
+    atomicAdd(dst + 1, wv.y);
+  }
 }
 
 void planted_lattice_bins(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
                           const double* anchors_dev, int nrhs, const LatticeDev& lat, int Luse,
-                          const BlueGeom& g, cplx* bins, int64_t bins_stride, cudaStream_t s) {
+                          const BlueGeom& g, cplx* bins, int64_t bins_stride, cplx* wts, cudaStream_t s) {
   if (s_count == 0) return;
   if (Luse == 0 || nrhs == 0) return;
-  MR1L_LAUNCH("planted_lattice_kernel", s, 0, 0,
-              planted_lattice_kernel<<<dim3(cdiv(s_count, 256), Luse, nrhs), 256, 0, s>>>(
-                  freqs, coeffs, s_count, d, t, anchors_dev, lat, g.off, bins, bins_stride));
+  // algorithmic bytes: every planted row and coefficient read once, the
+  // weights written and read once per lattice, one complex read-modify-write
+  // per (frequency, lattice, right-hand side)
+  MR1L_LAUNCH("planted_weights_kernel", s, 0, (double)s_count * (4.0 * (d - t) + 16.0 + 16.0 * nrhs),
+              planted_weights_kernel<<<dim3(cdiv(s_count, 256), nrhs), 256, 0, s>>>(freqs, coeffs, s_count, d, t,
+                                                                                     anchors_dev, wts));
+  MR1L_LAUNCH("planted_lattice_kernel", s, 0, (double)s_count * Luse * (4.0 * t + 48.0 * nrhs),
+              planted_lattice_kernel<<<dim3(cdiv(s_count, 256), Luse), 256, 0, s>>>(
+                  freqs, s_count, d, t, nrhs, wts, lat, g.off, bins, bins_stride));
 }
 
 // ---------------------------------------------------------------------------

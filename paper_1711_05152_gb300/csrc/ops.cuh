@@ -38,28 +38,32 @@ void residues(const CandSet& J, const LatticeDev& lat, cudaStream_t s);
 // bitmaps, offsets bm_off[l] in 32-bit words) and the coverage pass:
 // umask[c] = bitmask of lattices in which c is collision-free; cover[0] =
 // smallest L such that every covered c has a bit below L; cover[1] = number of
-// candidates in no I_l.  seen must be zeroed (2 * words) beforehand.
+// candidates in no I_l; cover[2 + l] = |I_l|; cover[66 + l] = candidates
+// whose first collision-free lattice is l (cover holds 130 ints).  seen must
+// be zeroed (2 * words) beforehand.
 void collide_and_cover(const CandSet& J, const LatticeDev& lat, uint32_t* seen, const int64_t* bm_off,
                        int64_t words, uint64_t* umask, int* cover, cudaStream_t s);
 
 // Algorithm 2 gather: p[h][c] = (1/cnt) sum_{l < Luse, c in I_l} w_l[r] C[h][off_l + r].
 // Also writes keys[h][c] = bits(re*re + im*im) (0 where uncovered) and
-// atomically maxes them into keymax[h] (must be zeroed beforehand).
+// atomically maxes them into keymax[h] (must be zeroed beforehand).  pairs =
+// sum_{l < Luse} |I_l| (launch accounting only).
 void gather(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
             const cplx* C, int64_t C_stride, int nrhs, cplx* p, int64_t p_stride, uint64_t* keys,
-            uint64_t* keymax, cudaStream_t s);
+            uint64_t* keymax, int64_t pairs, cudaStream_t s);
 
 // Scatter for evaluation: bins[h][off_l + r_l(c)] += weight, with weight c_k
 // (ADJOINT: c_k / (cnt_k M_l) for c in I_l only).  bins must be zeroed.
 void scatter(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
              const cplx* coef, int64_t coef_stride, int nrhs, int adjoint, cplx* bins, int64_t bins_stride,
-             cudaStream_t s);
+             int64_t pairs, cudaStream_t s);
 
 // Planted sampler, lattice request: weights c_h e^{2 pi i h_(>t).x'} per
 // right-hand side (anchors [nrhs][d]) scattered to bin h_(1..t).z_l mod M_l.
+// wts: device scratch of nrhs * s_count complex.
 void planted_lattice_bins(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t,
                           const double* anchors_dev, int nrhs, const LatticeDev& lat, int Luse,
-                          const BlueGeom& g, cplx* bins, int64_t bins_stride, cudaStream_t s);
+                          const BlueGeom& g, cplx* bins, int64_t bins_stride, cplx* wts, cudaStream_t s);
 
 // Planted sampler, line request: y[i][l] = p(x'_1.., l/K, ..x'_d) + noise.
 void planted_lines(const int32_t* freqs, const cplx* coeffs, int64_t s_count, int d, int t, int K,
@@ -104,15 +108,25 @@ struct SelectState {
   uint32_t hist[kSelBins];
 };
 
+// Segments of at most kSelSmallMax keys are selected by one CTA each in a
+// single launch; longer ones by the multi-CTA digit passes.
+constexpr int64_t kSelSmallMax = 65536;
+
 // Thresholded "(up to) cap largest" over nrhs segments of n keys each
 // (keys [h][n], keymax [h]); selected ids are OR-ed into flags[c] (uint8)
 // (shared across segments).  st: device SelectState [nrhs].
 void select_topk(const uint64_t* keys, int64_t n, int nrhs, const uint64_t* keymax, double theta2, int rel,
                  int64_t cap, SelectState* st, uint8_t* flags, cudaStream_t s);
 
+// Selection keys of plain values: keys[h][c] = bits(|p[h][c]|^2) + 1 where
+// eligible[c] != 0 (or eligible == nullptr), else 0; keymax[h] their maximum.
+void value_keys(const cplx* p, int64_t n, int nrhs, const uint8_t* eligible, uint64_t* keys, uint64_t* keymax,
+                cudaStream_t s);
+
 // Compaction of flags[c] into the next prefix list rows (pre x last) and,
-// optionally, the coefficients p[c].  Returns the count (synchronises).
+// optionally, the coefficients p[c].  Returns the count (synchronises);
+// total_host, if given, is pinned host memory for the count's copy.
 int64_t compact(const CandSet& J, const uint8_t* flags, int32_t* out_rows, const cplx* p, cplx* out_p,
-                int64_t* scratch_counts, int64_t scratch_len, cudaStream_t s);
+                int64_t* scratch_counts, int64_t scratch_len, int64_t* total_host, cudaStream_t s);
 
 }  // namespace mr1l

@@ -183,16 +183,172 @@ __global__ void sel_tie_kernel(const uint64_t* keys, int64_t n, const SelectStat
   }
 }
 
+// ---------------------------------------------------------------------------
+// The whole selection of a small segment in one CTA: the same six digit
+// passes, the pick of each digit by a block-wide suffix scan over the
+// shared-memory histogram, the marking and the tie pass.  One launch per
+// selection instead of nine, for segments whose keys one CTA reads six times
+// faster than nine dependent launches take to start.
+// ---------------------------------------------------------------------------
+constexpr int kSelSmallThreads = 1024;
+
+// Exclusive suffix sum over the threads of the block: the sum of v over all
+// threads with a larger index.  tmp: shared [kSelSmallThreads / 32].
+__device__ __forceinline__ uint32_t block_suffix_excl(uint32_t v, uint32_t* tmp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;  // inclusive suffix within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_down_sync(0xffffffffu, x, o);
+    if (lane + o < 32) x += y;
+  }
+  if (lane == 0) tmp[w] = x;  // the warp's total
+  __syncthreads();
+  uint32_t above = 0;
+  for (int u = w + 1; u < nw; ++u) above += tmp[u];
+  __syncthreads();
+  return above + x - v;
+}
+
+__global__ void __launch_bounds__(kSelSmallThreads) sel_small_kernel(const uint64_t* keys, int64_t n,
+                                                                      const uint64_t* keymax, double theta2, int rel,
+                                                                      int64_t cap, uint8_t* flags) {
+  __shared__ uint32_t hist[kSelBins];
+  __shared__ uint32_t tmp[kSelSmallThreads / 32];
+  __shared__ uint64_t s_prefix;
+  __shared__ int64_t s_need, s_eq;
+  __shared__ int s_all;
+  const int h = blockIdx.x;
+  const uint64_t* kh = keys + (int64_t)h * n;
+  double thr_d = theta2;
+  if (rel) {
+    const uint64_t km = keymax[h];
+    thr_d = theta2 * (km ? __longlong_as_double((long long)(km - 1)) : 0.0);
+  }
+  const uint64_t thr = (uint64_t)__double_as_longlong(thr_d) + 1;  // covered keys carry +1
+  if (threadIdx.x == 0) {
+    s_prefix = 0;
+    s_need = cap;
+    s_eq = 0;
+    s_all = 0;
+  }
+  for (int pass = 0; pass < kSelPasses; ++pass) {
+    int lo, width;
+    sel_digit(pass, lo, width);
+    const int nb = 1 << width;
+    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint64_t hi_mask = pass == 0 ? 0ull : (~0ull << (lo + width));
+    const uint64_t prefix = s_prefix & hi_mask;
+    for (int64_t c0 = 0; c0 < n; c0 += blockDim.x) {  // same trip count for every warp
+      const int64_t c = c0 + threadIdx.x;
+      int bin = -1;
+      if (c < n) {
+        const uint64_t k = kh[c];
+        if (k >= thr && (k & hi_mask) == prefix) bin = (int)((k >> lo) & (nb - 1));
+      }
+      const unsigned same = __match_any_sync(0xffffffffu, bin);
+      if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
+    }
+    __syncthreads();
+    // thread t owns bins 2t and 2t + 1; find the bin holding the need-th largest
+    const int b0 = 2 * threadIdx.x;
+    const uint32_t h0 = b0 < nb ? hist[b0] : 0, h1 = b0 + 1 < nb ? hist[b0 + 1] : 0;
+    const uint32_t above = block_suffix_excl(h0 + h1, tmp);
+    if (pass == 0) {
+      // the total number of eligible keys is the suffix sum above thread -1
+      if (threadIdx.x == 0 && (int64_t)(above + h0 + h1) <= cap) s_all = 1;
+      __syncthreads();
+      if (s_all) break;
+    }
+    const int64_t need = s_need;
+    __syncthreads();
+    if ((int64_t)above < need && (int64_t)(above + h0 + h1) >= need) {
+      if ((int64_t)above + h1 >= need) {
+        s_prefix |= (uint64_t)(b0 + 1) << lo;
+        s_need = need - above;
+        s_eq = h1;
+      } else {
+        s_prefix |= (uint64_t)b0 << lo;
+        s_need = need - above - h1;
+        s_eq = h0;
+      }
+    }
+    __syncthreads();
+  }
+  const bool all = s_all;
+  const uint64_t T = s_prefix;
+  const int64_t need = s_need;
+  const bool eq_all = need == s_eq;
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    const uint64_t k = kh[c];
+    if (k >= thr && (all || k > T || (k == T && eq_all))) flags[c] = 1;
+  }
+  if (all || eq_all) return;
+  // more keys equal to the cut than still needed: the smallest ids among them
+  int64_t base = 0;
+  for (int64_t c0 = 0; c0 < n && base < need; c0 += blockDim.x) {
+    const int64_t c = c0 + threadIdx.x;
+    const bool e = c < n && kh[c] == T;
+    const unsigned b = __ballot_sync(0xffffffffu, e);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) tmp[w] = __popc(b);
+    __syncthreads();
+    int64_t pos = base + __popc(b & ((1u << lane) - 1));
+    for (int u = 0; u < w; ++u) pos += tmp[u];
+    if (e && pos < need) flags[c] = 1;
+    int64_t tot = 0;
+    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) tot += tmp[u];
+    __syncthreads();
+    base += tot;
+  }
+}
+
 void select_topk(const uint64_t* keys, int64_t n, int nrhs, const uint64_t* keymax, double theta2, int rel,
                  int64_t cap, SelectState* st, uint8_t* flags, cudaStream_t s) {
-  if (n == 0 || nrhs == 0) return;
+  if (n == 0 || nrhs == 0 || cap <= 0) return;
+  if (n <= kSelSmallMax) {
+    MR1L_LAUNCH("sel_small_kernel", s, 0, 8.0 * n * nrhs * (kSelPasses + 1),
+                sel_small_kernel<<<nrhs, kSelSmallThreads, 0, s>>>(keys, n, keymax, theta2, rel, cap, flags));
+    return;
+  }
   MR1L_LAUNCH("sel_init_kernel", s, 0, 0, sel_init_kernel<<<nrhs, 256, 0, s>>>(st, keymax, theta2, rel, nrhs));
   int blocks = (int)std::min<int64_t>(cdiv(n, 2048), 304);
   for (int pass = 0; pass < kSelPasses; ++pass)
     MR1L_LAUNCH("sel_hist_kernel", s, 0, 8.0 * n * nrhs,
                 sel_hist_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, pass, cap));
-  MR1L_LAUNCH("sel_mark_kernel", s, 0, 0, sel_mark_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, flags));
+  MR1L_LAUNCH("sel_mark_kernel", s, 0, 8.0 * n * nrhs,
+              sel_mark_kernel<<<dim3(blocks, nrhs), 256, 0, s>>>(keys, n, st, flags));
   MR1L_LAUNCH("sel_tie_kernel", s, 0, 0, sel_tie_kernel<<<nrhs, 1024, 0, s>>>(keys, n, st, flags));
+}
+
+// keys[h][c] = bits(re*re + im*im) + 1 (no fused multiply-add) where c is
+// eligible, else 0; keymax[h] = the largest key of segment h (zeroed first)
+__global__ void keys_kernel(const cplx* p, int64_t n, const uint8_t* eligible, uint64_t* keys, uint64_t* keymax) {
+  const int h = blockIdx.y;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  uint64_t key = 0;
+  if (c < n) {
+    if (!eligible || eligible[c]) {
+      const cplx v = p[(int64_t)h * n + c];
+      key = (uint64_t)__double_as_longlong(__dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y))) + 1;
+    }
+    keys[(int64_t)h * n + c] = key;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t u = __shfl_xor_sync(0xffffffffu, key, o);
+    key = u > key ? u : key;
+  }
+  if ((threadIdx.x & 31) == 0 && key) atomicMax((unsigned long long*)(keymax + h), (unsigned long long)key);
+}
+
+void value_keys(const cplx* p, int64_t n, int nrhs, const uint8_t* eligible, uint64_t* keys, uint64_t* keymax,
+                cudaStream_t s) {
+  MR1L_CUDA(cudaMemsetAsync(keymax, 0, nrhs * sizeof(uint64_t), s));
+  if (n == 0 || nrhs == 0) return;
+  MR1L_LAUNCH("keys_kernel", s, 0, (double)nrhs * n * 24.0 + (eligible ? (double)n : 0.0),
+              keys_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(p, n, eligible, keys, keymax));
 }
 
 // ---------------------------------------------------------------------------
@@ -253,20 +409,22 @@ __global__ void compact_scatter_kernel(CandSet J, const uint8_t* flags, const in
 }
 
 int64_t compact(const CandSet& J, const uint8_t* flags, int32_t* out_rows, const cplx* p, cplx* out_p,
-                int64_t* scratch_counts, int64_t scratch_len, cudaStream_t s) {
+                int64_t* scratch_counts, int64_t scratch_len, int64_t* total_host, cudaStream_t s) {
   const int64_t n = J.n();
   if (n == 0) return 0;
   const int64_t nblocks = cdiv(n, kCompactBlock);
   MR1L_REQUIRE(scratch_len >= nblocks + 1, "compaction scratch too small");
-  MR1L_LAUNCH("compact_count_kernel", s, 0, 0, compact_count_kernel<<<nblocks, kCompactBlock, 0, s>>>(flags, n, scratch_counts));
+  MR1L_LAUNCH("compact_count_kernel", s, 0, (double)n + 8.0 * nblocks,
+              compact_count_kernel<<<nblocks, kCompactBlock, 0, s>>>(flags, n, scratch_counts));
   MR1L_LAUNCH("compact_scan_kernel", s, 0, 0, compact_scan_kernel<<<1, kCompactBlock, 0, s>>>(scratch_counts, nblocks));
   if (out_rows || out_p) {
     MR1L_LAUNCH("compact_scatter_kernel", s, 0, 0, compact_scatter_kernel<<<nblocks, kCompactBlock, 0, s>>>(J, flags, scratch_counts, out_rows, p, out_p));
   }
-  int64_t total = 0;
-  MR1L_CUDA(cudaMemcpyAsync(&total, scratch_counts + nblocks, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  int64_t local = 0;
+  int64_t* total = total_host ? total_host : &local;
+  MR1L_CUDA(cudaMemcpyAsync(total, scratch_counts + nblocks, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   MR1L_CUDA(cudaStreamSynchronize(s));
-  return total;
+  return *total;
 }
 
 }  // namespace mr1l

@@ -106,3 +106,35 @@ def test_theorem_params(lib):
     assert r2 > r1 and b2 >= b1
     with pytest.raises(P.Mr1lError):
         P.theorem_params(5, 1000, 1.5)
+
+
+def test_output_tensor_checks():
+    """Output tensors written through raw pointers are refused unless they
+    have exactly the expected shape, dtype and device (checked on the host,
+    before any launch)."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cpu")
+    P.check_out(torch.empty((2, 5), dtype=torch.complex128), (2, 5), dev)
+    with pytest.raises(ValueError, match="shape"):
+        P.check_out(torch.empty((2, 4), dtype=torch.complex128), (2, 5), dev)
+    with pytest.raises(ValueError, match="shape"):
+        P.check_out(torch.empty((1, 5), dtype=torch.complex128), (2, 5), dev)
+    with pytest.raises(TypeError):
+        P.check_out(torch.empty((2, 5), dtype=torch.complex64), (2, 5), dev)
+    with pytest.raises(TypeError):
+        P.check_out(torch.empty((5, 2), dtype=torch.complex128).t(), (2, 5), dev)
+    with pytest.raises(ValueError, match="expected cuda"):
+        P.check_out(torch.empty((2, 5), dtype=torch.complex128), (2, 5), torch.device("cuda", 0))
+
+
+def test_pool_stats_and_injection_controls(lib):
+    """The block-cache counters and the allocation-failure injector are host
+    calls: they work without a GPU."""
+    st = P.pool_stats(63)
+    assert st == {"outstanding": 0, "cached": 0, "mallocs": 0}
+    P.inject_alloc_failure(5)
+    P.inject_alloc_failure(-1)
+    with pytest.raises(P.Mr1lError):
+        P.inject_alloc_failure(-2)
+    with pytest.raises(P.Mr1lError):
+        P.pool_stats(-1)

@@ -45,23 +45,3 @@ def test_batch_small_parity():
     outs = P.sfft_dimincr_batch(probs, concurrency=4)
     for out, ref in zip(outs, refs):
         _assert_equal(out, ref)
-
-
-def test_batch_256_signals():
-    """The 256-signal workload (d in 5..12, N in {16, 32, 64}, s log-uniform
-    in [100, 2000], noiseless, r = 3): every signal's planted support is
-    recovered with machine-precision coefficients, and three sampled signals
-    (the two cheapest and the median by d s N) match the oracle bit for bit."""
-    batch = W.batch_signals(256, seed=1)
-    probs = [_problem(sig, prm, 1000 + i) for i, (sig, prm) in enumerate(batch)]
-    outs = P.sfft_dimincr_batch(probs, concurrency=16)
-    for (sig, prm), out in zip(batch, outs):
-        np.testing.assert_array_equal(out.freqs, sig.freqs.astype(np.int64))
-        assert np.max(np.abs(out.coeffs - sig.coeffs) / np.abs(sig.coeffs)) < 1e-10
-    cost = [sig.d * prm["s"] * (2 * sig.N + 1) for sig, prm in batch]
-    order = np.argsort(cost)
-    for i in (int(order[0]), int(order[1]), int(order[len(order) // 2])):
-        sig, prm = batch[i]
-        ref = sfft.sfft(sig, prm["s"], prm["s_local"], prm["r"], prm["b"], prm["theta"], prm["theta_mode"],
-                        seed=1000 + i)
-        _assert_equal(outs[i], ref)

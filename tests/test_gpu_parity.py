@@ -312,3 +312,40 @@ def test_batched_plans_match_single_calls():
     for pl, y, c, g, ge in zip(plans, ys, cs, got, gote):
         np.testing.assert_array_equal(g.cpu().numpy(), pl.reconstruct(y).cpu().numpy())
         np.testing.assert_array_equal(ge.cpu().numpy(), pl.evaluate(c, P.MR1L_ADJOINT).cpu().numpy())
+
+
+@pytest.mark.parametrize("n,t,N", [(7, 1, 4), (50, 2, 5), (333, 3, 6), (1500, 4, 8), (9000, 5, 9)])
+def test_plan_search_redraw_bitexact(n, t, N):
+    """Algorithm 1 with the redraw rule (the remark after it): the same
+    lattices, generating vectors and collision-free sets as the oracle."""
+    rng = np.random.default_rng(n + 1)
+    J = _rand_set(rng, n, t, N)
+    for seed in range(3):
+        ml = lattice.search(J, seed=seed, t=t, redraw=True)
+        pl = P.plan_search(J, seed=seed, redraw=True)
+        assert pl.L == ml.L and list(pl.M) == ml.M
+        np.testing.assert_array_equal(pl.z, np.stack(ml.z))
+        masks, _ = pl.masks()
+        want_mask = np.zeros(J.shape[0], dtype=np.uint64)
+        for l, IL in enumerate(ml.unique):
+            want_mask |= IL.astype(np.uint64) << np.uint64(l)
+        np.testing.assert_array_equal(masks, want_mask)
+
+
+@pytest.mark.parametrize("name,seed", [("tiny_d3", 11), ("tiny_d3", 12)])
+def test_sfft_redraw_parity(name, seed):
+    sig, p = W.workload(name, seed)
+    out = P.sfft_dimincr(sig.d, sig.N, p["s"], p["r"], p["theta"], p["theta_mode"], seed=seed, b=p["b"],
+                         freqs=sig.freqs, coeffs=sig.coeffs, sigma=sig.sigma, redraw=True)
+    ref = sfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=seed, redraw=True)
+    _assert_sfft_equal(out, ref)
+
+
+def test_sfft_redraw_parity_d6():
+    """A six-dimensional planted signal (noisy) with the redraw rule, and
+    its sample count at most the plain rule's."""
+    sig = W.planted_signal(6, 12, 150, seed=13, model="u1_10", snr_db=30.0)
+    out = P.sfft_dimincr(6, 12, 150, 3, 1e-12, "rel", seed=13, freqs=sig.freqs, coeffs=sig.coeffs,
+                         sigma=sig.sigma, redraw=True, batch_reps=True)
+    ref = sfft.sfft(sig, 150, 150, 3, 10, 1e-12, "rel", seed=13, redraw=True)
+    _assert_sfft_equal(out, ref)

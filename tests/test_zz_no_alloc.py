@@ -1,8 +1,9 @@
 """mr1l_reconstruct_noalloc: Algorithm 2 for callers that cannot allocate
 device memory while they run (their device memory is owned by another
 allocator or budget, or they cannot afford the synchronisation an allocation
-may cause).  Its result must equal mr1l_reconstruct's; it is called twice in
-a row with different inputs, since every call reuses the same fixed scratch."""
+may cause).  Its result must equal mr1l_reconstruct's (and the CPU oracle's);
+it is called twice in a row with different inputs, since every call reuses
+the same fixed scratch, and the second call must take no device memory."""
 
 import ctypes
 
@@ -12,6 +13,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import paper_1711_05152_gb300 as P
+from oracle import lattice
 
 pytestmark = pytest.mark.gpu
 
@@ -25,6 +27,9 @@ def test_reconstruct_noalloc_matches_reconstruct():
     rng = np.random.default_rng(21)
     J = np.unique(rng.integers(-8, 9, size=(4000, 4)), axis=0)[:3000]
     pl = P.plan_search(J, seed=22)
+    ml = lattice.search(J.astype(np.int64), seed=22, t=J.shape[1])
+    assert list(pl.M) == ml.M
+    dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream().cuda_stream
     nrhs = 2
     for call in range(2):
@@ -32,12 +37,22 @@ def test_reconstruct_noalloc_matches_reconstruct():
         y = y.cuda()
         want = pl.reconstruct(y)
         got = torch.full_like(want, complex(np.nan, np.nan))
+        torch.cuda.synchronize()
+        pool0, free0 = P.pool_stats(dev), torch.cuda.mem_get_info()[0]
         rc = lib.mr1l_reconstruct_noalloc(pl._h, ctypes.c_void_p(y.data_ptr()), nrhs,
                                           ctypes.c_void_p(got.data_ptr()), ctypes.c_void_p(stream))
         assert rc == P.MR1L_OK
         torch.cuda.synchronize()
+        if call == 1:
+            # the first call may load the library's device code and commit the
+            # fixed array; from then on a call takes no device memory at all
+            assert P.pool_stats(dev) == pool0
+            assert torch.cuda.mem_get_info()[0] == free0
         w, g = want.cpu().numpy(), got.cpu().numpy()
         assert np.max(np.abs(g - w)) / np.max(np.abs(w)) < RTOL, f"call {call}"
+        # and against the CPU oracle's Algorithm 2 on the first right-hand side
+        ref, _ = lattice.reconstruct(J.astype(np.int64), ml, np.split(y[0].cpu().numpy(), np.cumsum(ml.M)[:-1]))
+        assert np.max(np.abs(g[0] - ref)) / np.max(np.abs(ref)) < RTOL, f"call {call} against the oracle"
 
 
 def test_reconstruct_noalloc_rejects_oversize():
