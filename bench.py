@@ -760,7 +760,7 @@ def _run_stats(problems, sigs, fft, concurrency=16):
         correct.append(len(set(truth) & set(got)))
         success.append(set(truth) == set(got))
         err.append(float(np.sqrt(num / sum(abs(c) ** 2 for c in truth.values()))))
-    return {"max_samples": int(max(samples)), "min_correct": int(min(correct)),
+    return {"max_samples": int(max(samples)), "mean_samples": float(np.mean(samples)), "min_correct": int(min(correct)),
             "success_rate": float(np.mean(success)), "max_rel_l2": float(max(err))}
 
 
@@ -810,10 +810,12 @@ def run_paper_table(args):
             t0 = time.time()
             sigs = [W.planted_signal(d, 32, supp, seed=base + i, model="box") for i in range(reps)]
             probs = [dict(d=d, N=32, s=supp, s_local=supp, r=1, b=10, theta=1e-12, theta_mode="abs",
-                          seed=base + i, freqs=g.freqs, coeffs=g.coeffs) for i, g in enumerate(sigs)]
+                          seed=base + i, freqs=g.freqs, coeffs=g.coeffs, redraw=args.redraw)
+                     for i, g in enumerate(sigs)]
             # |supp| = 1e5 solves hold about 25 GB of device buffers each: two at a time
             st = _run_stats(probs, sigs, args.fft, concurrency=16 if supp < 100000 else 2)
-            print(json.dumps({"paper_table": "5.1", "d": d, "supp": supp, "reps": reps, "fft": args.fft, **st,
+            print(json.dumps({"paper_table": "5.1", "d": d, "supp": supp, "reps": reps, "fft": args.fft,
+                              "redraw": args.redraw, **st,
                               "paper": {"max_samples": int(pmax), "max_rel_l2": perr},
                               "samples_over_paper": st["max_samples"] / pmax,
                               "seconds": round(time.time() - t0, 2)}), flush=True)
@@ -860,23 +862,33 @@ def run_paper_table(args):
 
 
 def run_kernel_case(args):
-    """The lattice transform alone at the bench workload's size (|J| = 65 x
-    1000 candidates in Z^10, Algorithm 1 lattice, 5 right-hand sides): one
-    warm-up and one measured reconstruct + adjoint, for ncu captures."""
+    """The lattice transform alone at a workload-like size: |J| = 65 x
+    `--kc-prefix` candidates in Z^10 (a prefix set times the 65 values of the
+    last component, as in the d = 10 workload), its Algorithm 1 lattice and 5
+    right-hand sides: one warm-up and one measured reconstruct + adjoint, then
+    the memory-bound steps around them on data of the same size (the
+    selection of the 5 coefficient vectors, a small-segment selection, the
+    lattice noise of the 5 passes).  For ncu captures."""
     import torch
 
     import paper_1711_05152_gb300 as P
     rng = np.random.default_rng(args.seed)
-    pre = np.unique(rng.integers(-32, 33, size=(1100, 9)), axis=0)[:1000]
-    J = np.concatenate([np.repeat(pre, 65, axis=0), np.tile(np.arange(-32, 33), 1000)[:, None]], axis=1)
+    npre = args.kc_prefix
+    pre = np.unique(rng.integers(-32, 33, size=(npre + npre // 10 + 10, 9)), axis=0)[:npre]
+    J = np.concatenate([np.repeat(pre, 65, axis=0), np.tile(np.arange(-32, 33), npre)[:, None]], axis=1)
     pl = P.plan_search(J, seed=args.seed, fft=args.fft)
     y = torch.from_numpy(W.complex_normal(rng, (5, pl.sum_M))).cuda()
     for _ in range(2):
         c = pl.reconstruct(y)
         pl.evaluate(c, P.MR1L_ADJOINT)
+    for _ in range(2):
+        P.select(c, 1000, 1e-12, "rel")
+        P.select(c[:, :50000].contiguous(), 1000, 1e-12, "rel")
+        for h in range(5):
+            P.lattice_noise(args.seed, 5, h, pl.M, 1.0)
     torch.cuda.synchronize()
-    print(json.dumps({"kernel_case": "reconstruct+adjoint", "fft": args.fft, "n": int(J.shape[0]), "L": pl.L,
-                      "sum_M": int(pl.sum_M), "M0": int(pl.M[0])}))
+    print(json.dumps({"kernel_case": "reconstruct+adjoint, selections, noise", "fft": args.fft, "n": int(J.shape[0]),
+                      "L": pl.L, "sum_M": int(pl.sum_M), "M0": int(pl.M[0])}))
     return 0
 
 
@@ -893,12 +905,16 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads of the default line")
     ap.add_argument("--no-fast-fft", action="store_true", help="skip the double-float FFT form")
     ap.add_argument("--fft", default="f64", choices=["f64", "df"], help="arithmetic of --kernel-case and --paper-table")
+    ap.add_argument("--kc-prefix", type=int, default=1000,
+                    help="prefix rows of the --kernel-case candidate set (|J| = 65 x this)")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the lattice transform at the workload size (for ncu captures)")
     ap.add_argument("--paper-table", choices=["5.1", "5.2", "5.4", "5.7"],
                     help="rerun one of the paper's statistical experiments on the GPU path")
     ap.add_argument("--reps", type=int, default=10, help="repetitions per row of --paper-table")
     ap.add_argument("--sizes", default="1000,10000", help="sparsities of the --paper-table 5.1 rows")
+    ap.add_argument("--redraw", action="store_true",
+                    help="--paper-table 5.1 with the redraw rule of Algorithm 1 (the remark after it)")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)

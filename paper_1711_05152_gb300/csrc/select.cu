@@ -95,6 +95,26 @@ __device__ void sel_pick(SelectState& S, int64_t cap, int pass) {
   if (t == 0) S.ticket = 0;
 }
 
+// One round of digit counting: kSelUnroll keys per thread at c0 + threadIdx.x
+// + u * stride (keys past n count as 0, which is below every threshold).
+constexpr int kSelUnroll = 8;
+__device__ __forceinline__ void sel_count_round(const uint64_t* kh, int64_t n, int64_t c0, int64_t stride,
+                                                uint64_t thr, uint64_t hi_mask, uint64_t prefix, int lo, int nb,
+                                                uint32_t* hist) {
+  uint64_t k[kSelUnroll];
+#pragma unroll
+  for (int u = 0; u < kSelUnroll; ++u) {
+    const int64_t c = c0 + threadIdx.x + u * stride;
+    k[u] = c < n ? kh[c] : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < kSelUnroll; ++u) {
+    const int bin = (k[u] >= thr && (k[u] & hi_mask) == prefix) ? (int)((k[u] >> lo) & (nb - 1)) : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, bin);
+    if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
+  }
+}
+
 __global__ void __launch_bounds__(256) sel_hist_kernel(const uint64_t* keys, int64_t n, SelectState* st, int pass,
                                                        int64_t cap) {
   __shared__ uint32_t hist[kSelBins];
@@ -112,18 +132,12 @@ __global__ void __launch_bounds__(256) sel_hist_kernel(const uint64_t* keys, int
   const uint64_t prefix = S.prefix & hi_mask;
   const uint64_t* kh = keys + h * n;
   // keys of similar magnitude share the top digits, so the lanes of a warp
-  // that hit the same bin are merged into one shared-memory atomic
+  // that hit the same bin are merged into one shared-memory atomic; the keys
+  // of kSelUnroll rounds are loaded before any is counted, so their loads
+  // are in flight together
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x; c0 < n; c0 += stride) {  // same trip count per warp
-    const int64_t c = c0 + threadIdx.x;
-    int bin = -1;
-    if (c < n) {
-      const uint64_t k = kh[c];
-      if (k >= thr && (k & hi_mask) == prefix) bin = (int)((k >> lo) & (nb - 1));
-    }
-    const unsigned same = __match_any_sync(0xffffffffu, bin);
-    if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
-  }
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x; c0 < n; c0 += stride * kSelUnroll)  // same trip count per warp
+    sel_count_round(kh, n, c0, stride, thr, hi_mask, prefix, lo, nb, hist);
   __syncthreads();
   for (int i = threadIdx.x; i < nb; i += blockDim.x)
     if (hist[i]) atomicAdd(&S.hist[i], hist[i]);
@@ -240,16 +254,8 @@ __global__ void __launch_bounds__(kSelSmallThreads) sel_small_kernel(const uint6
     __syncthreads();
     const uint64_t hi_mask = pass == 0 ? 0ull : (~0ull << (lo + width));
     const uint64_t prefix = s_prefix & hi_mask;
-    for (int64_t c0 = 0; c0 < n; c0 += blockDim.x) {  // same trip count for every warp
-      const int64_t c = c0 + threadIdx.x;
-      int bin = -1;
-      if (c < n) {
-        const uint64_t k = kh[c];
-        if (k >= thr && (k & hi_mask) == prefix) bin = (int)((k >> lo) & (nb - 1));
-      }
-      const unsigned same = __match_any_sync(0xffffffffu, bin);
-      if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
-    }
+    for (int64_t c0 = 0; c0 < n; c0 += (int64_t)blockDim.x * kSelUnroll)  // same trip count for every warp
+      sel_count_round(kh, n, c0, blockDim.x, thr, hi_mask, prefix, lo, nb, hist);
     __syncthreads();
     // thread t owns bins 2t and 2t + 1; find the bin holding the need-th largest
     const int b0 = 2 * threadIdx.x;

@@ -349,3 +349,25 @@ def test_sfft_redraw_parity_d6():
                          sigma=sig.sigma, redraw=True, batch_reps=True)
     ref = sfft.sfft(sig, 150, 150, 3, 10, 1e-12, "rel", seed=13, redraw=True)
     _assert_sfft_equal(out, ref)
+
+
+@pytest.mark.parametrize("density", [0.003, 0.03, 0.1, 0.3])
+@pytest.mark.parametrize("fft", ["f64", "df"])
+def test_evaluate_sparse_coefficients(density, fft):
+    """Lattice evaluation of sparse coefficient vectors, where the evaluation
+    column pass sums the few non-zeros of each column directly (plain sums
+    for one or two, the split by n1 mod 8 for three to 24, the column FFT in
+    tiles holding a denser column): against the oracle, normwise and at
+    every sample that a single coefficient would make non-zero."""
+    rng = np.random.default_rng(int(density * 1e4))
+    J = _rand_set(rng, 40000, 6, 10)
+    pl = P.plan_search(J, seed=41, fft=fft)
+    ml = lattice.search(J, seed=41, t=6)
+    c = np.zeros((2, J.shape[0]), dtype=np.complex128)
+    for h in range(2):
+        k = rng.random(J.shape[0]) < density
+        c[h, k] = rng.standard_normal(k.sum()) + 1j * rng.standard_normal(k.sum())
+    got = pl.evaluate(torch.from_numpy(c).cuda(), P.MR1L_EVAL).cpu().numpy()
+    for h in range(2):
+        want = np.concatenate(lattice.evaluate(J, ml, c[h], "eval", "fft"))
+        assert _normwise(got[h], want) < RTOL
