@@ -865,10 +865,12 @@ def run_kernel_case(args):
     """The lattice transform alone at a workload-like size: |J| = 65 x
     `--kc-prefix` candidates in Z^10 (a prefix set times the 65 values of the
     last component, as in the d = 10 workload), its Algorithm 1 lattice and 5
-    right-hand sides: one warm-up and one measured reconstruct + adjoint, then
-    the memory-bound steps around them on data of the same size (the
-    selection of the 5 coefficient vectors, a small-segment selection, the
-    lattice noise of the 5 passes).  For ncu captures."""
+    right-hand sides: one warm-up and one measured reconstruct + adjoint, two
+    evaluations of sparse coefficient vectors (every 35th and every 400th
+    coefficient kept, as in the planted sampler), then the memory-bound steps
+    around them on data of the same size (the selection of the 5 coefficient
+    vectors, a small-segment selection, the lattice noise of the 5 passes).
+    For ncu captures."""
     import torch
 
     import paper_1711_05152_gb300 as P
@@ -881,6 +883,13 @@ def run_kernel_case(args):
     for _ in range(2):
         c = pl.reconstruct(y)
         pl.evaluate(c, P.MR1L_ADJOINT)
+    # sparse evaluations (as in the planted sampler): about 8 and 1 non-zero
+    # bins per column of the evaluation column pass
+    for keep in (35, 400):
+        cs = torch.zeros_like(c)
+        cs[:, ::keep] = c[:, ::keep]
+        for _ in range(2):
+            pl.evaluate(cs, P.MR1L_EVAL)
     for _ in range(2):
         P.select(c, 1000, 1e-12, "rel")
         P.select(c[:, :50000].contiguous(), 1000, 1e-12, "rel")

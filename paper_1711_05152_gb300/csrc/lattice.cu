@@ -470,11 +470,13 @@ __global__ void planted_line_eval_kernel(const cplx* bins, int K, int t, double 
   __syncthreads();
   for (int l = threadIdx.x; l < K; l += blockDim.x) {
     cplx acc = cmake(0.0, 0.0);
+    int m = 0;  // l r mod K, advanced by l per step
     for (int r = 0; r < K; ++r) {
-      int m = (int)(((int64_t)l * r) % K);
       cplx v = cmul(B[r], ph[m]);
       acc.x += v.x;
       acc.y += v.y;
+      m += l;
+      if (m >= K) m -= K;
     }
     if (noise_scale != 0.0) {
       U64Pair u = philox_u64(noise_seed, kNoiseLine, (uint32_t)t, (uint32_t)l, 0u, (uint32_t)(rep0 + i));
@@ -527,11 +529,13 @@ __global__ void detect_lines_kernel(const cplx* y, int N, int64_t cap, double th
     int k = a - N;
     int km = k < 0 ? k + K : k;
     cplx acc = cmake(0.0, 0.0);
+    int m = 0;  // km l mod K, advanced by km per step
     for (int l = 0; l < K; ++l) {
-      int m = (int)(((int64_t)km * l) % K);
       cplx v = cmul(Y[l], ph[m]);
       acc.x += v.x;
       acc.y += v.y;
+      m += km;
+      if (m >= K) m -= K;
     }
     double re = acc.x / (double)K, im = acc.y / (double)K;
     double k2 = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
