@@ -1,7 +1,8 @@
 """The large workload (d = 25, N = 32, s = 10^4, log-uniform amplitudes in
 [1e-2, 10], 20 dB noise, r = 10 repetitions fused per increment).
 
-The oracle cannot finish the whole run in test time, so the check is split:
+The oracle needs about an hour for the whole run (tests/test_gpu_oracle_runs.py
+compares the GPU with its stored complete run); here
 the first increments (t <= 3, where |J_3| = 274,625 candidates and each
 lattice has about 5.5e5 nodes) are compared with the oracle bit for bit, and
 the full run is checked against what the planted signal fixes at any size."""
@@ -61,3 +62,19 @@ def test_large_full_run_properties():
             assert abs(c) < 8 * noise
     strong = [f for f, c in truth.items() if abs(c) > 20 * noise]
     assert all(f in got for f in strong)
+
+
+@pytest.mark.slow
+def test_large_first_increments_redraw_match_oracle():
+    """The redraw rule of Algorithm 1 at the large workload's sizes (|J_3| =
+    274,625 candidates): the first increments against the oracle."""
+    sig, p = W.workload("large_d25", 1)
+    out = P.sfft_dimincr(sig.d, sig.N, p["s"], p["r"], p["theta"], p["theta_mode"], seed=1, b=p["b"],
+                         freqs=sig.freqs, coeffs=sig.coeffs, sigma=sig.sigma, batch_reps=True, t_stop=3, redraw=True)
+    ref = sfft.sfft(sig, p["s"], p["s_local"], p["r"], p["b"], p["theta"], p["theta_mode"], seed=1, t_stop=3,
+                    redraw=True)
+    assert min(st.min_gap_rank for st in ref.steps) > 1e-9, "degenerate seed (near tie)"
+    for st, rs in zip(out.steps, ref.steps):
+        assert (st["n_line"], st["n_cand"], st["L"], st["attempts"], st["samples"]) == \
+            (rs.I_t, rs.n_candidates, rs.L, rs.attempts, rs.samples)
+    np.testing.assert_array_equal(out.freqs, ref.freqs)

@@ -82,3 +82,20 @@ def test_batch256_all_signals_match_oracle():
         # the oracle's coefficients: the planted ones plus the stored offsets
         ref = sig.coeffs + z["delta"][off[i]:off[i + 1]].astype(np.complex128)
         assert np.max(np.abs(out.coeffs - ref) / np.abs(ref)) < RTOL, f"signal {i}"
+
+
+@pytest.mark.slow
+def test_large_d25_complete_run_double_float_matches_oracle():
+    """The same complete run with the Bluestein butterflies in double-float
+    arithmetic (MR1L_FFT_DF): the same increments and set, and coefficients
+    within the same 1e-10 of the oracle's FP64 values."""
+    z = np.load(LARGE)
+    assert z["step_min_gap_rank"].min() > GAP and z["step_min_gap_thr"].min() > GAP, "degenerate seed (near tie)"
+    sig, p = W.workload("large_d25", 1)
+    out = P.sfft_dimincr(sig.d, sig.N, p["s"], p["r"], p["theta"], p["theta_mode"], seed=1, s_local=p["s_local"],
+                         b=p["b"], freqs=sig.freqs, coeffs=sig.coeffs, sigma=sig.sigma, batch_reps=True, fft="df")
+    assert [st["L"] for st in out.steps] == z["step_L"].tolist()
+    np.testing.assert_array_equal(out.freqs, z["freqs"].astype(np.int64))
+    assert out.samples == int(z["samples"])
+    ref = z["coeffs"]
+    assert np.max(np.abs(out.coeffs - ref) / np.abs(ref)) < RTOL
