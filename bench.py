@@ -864,8 +864,8 @@ def run_paper_table(args):
 def run_kernel_case(args):
     """The lattice transform alone at a workload-like size: |J| = 65 x
     `--kc-prefix` candidates in Z^10 (a prefix set times the 65 values of the
-    last component, as in the d = 10 workload), its Algorithm 1 lattice and 5
-    right-hand sides: one warm-up and one measured reconstruct + adjoint, two
+    last component, as in the d = 10 workload), its Algorithm 1 lattice and
+    `--kc-rhs` right-hand sides (5): one warm-up and one measured reconstruct + adjoint, two
     evaluations of sparse coefficient vectors (every 35th and every 400th
     coefficient kept, as in the planted sampler), then the memory-bound steps
     around them on data of the same size (the selection of the 5 coefficient
@@ -879,7 +879,7 @@ def run_kernel_case(args):
     pre = np.unique(rng.integers(-32, 33, size=(npre + npre // 10 + 10, 9)), axis=0)[:npre]
     J = np.concatenate([np.repeat(pre, 65, axis=0), np.tile(np.arange(-32, 33), npre)[:, None]], axis=1)
     pl = P.plan_search(J, seed=args.seed, fft=args.fft)
-    y = torch.from_numpy(W.complex_normal(rng, (5, pl.sum_M))).cuda()
+    y = torch.from_numpy(W.complex_normal(rng, (args.kc_rhs, pl.sum_M))).cuda()
     for _ in range(2):
         c = pl.reconstruct(y)
         pl.evaluate(c, P.MR1L_ADJOINT)
@@ -893,7 +893,7 @@ def run_kernel_case(args):
     for _ in range(2):
         P.select(c, 1000, 1e-12, "rel")
         P.select(c[:, :50000].contiguous(), 1000, 1e-12, "rel")
-        for h in range(5):
+        for h in range(args.kc_rhs):
             P.lattice_noise(args.seed, 5, h, pl.M, 1.0)
     torch.cuda.synchronize()
     print(json.dumps({"kernel_case": "reconstruct+adjoint, selections, noise", "fft": args.fft, "n": int(J.shape[0]),
@@ -916,6 +916,7 @@ def main():
     ap.add_argument("--fft", default="f64", choices=["f64", "df"], help="arithmetic of --kernel-case and --paper-table")
     ap.add_argument("--kc-prefix", type=int, default=1000,
                     help="prefix rows of the --kernel-case candidate set (|J| = 65 x this)")
+    ap.add_argument("--kc-rhs", type=int, default=5, help="right-hand sides of the --kernel-case transforms")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the lattice transform at the workload size (for ncu captures)")
     ap.add_argument("--paper-table", choices=["5.1", "5.2", "5.4", "5.7"],
