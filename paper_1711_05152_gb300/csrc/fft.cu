@@ -296,9 +296,21 @@ __device__ __forceinline__ void twiddled_dft(typename O::V* v, int n, int Ns, in
 //   else: element index fastest (row tiles, is == 1)
 // HALF (first radix-8 stage only): inputs r >= 4 are known zeros.
 // ---------------------------------------------------------------------------
+// Shared-memory tiles of the 4-step passes are stored swizzled: element e of
+// a tile at e ^ ((e >> 3) & 7).  The first stage of a sub-FFT writes 8
+// consecutive elements per thread, a 128-byte stride between the lanes of a
+// warp when a tile holds one sequence, which unswizzled hits one 16-byte bank
+// group 8 times per 128-byte wavefront; the swizzle spreads those lanes over
+// the 8 groups and only permutes elements within each aligned group of 8, so
+// the stride-1 accesses of the other stages stay conflict-free.  (Tiles hold
+// a multiple of 8 elements.)
+__device__ __forceinline__ int tile_swz(int e) { return e ^ ((e >> 3) & 7); }
+
 template <int R, bool INV, bool COLS, class O, bool HALF = false>
 __device__ __forceinline__ void stockham_stage(typename O::V* s, int n, int Ns, int nseq, int bs, int is,
                                                const typename O::V* twn_n, const cplx* ft) {
+  // COLS tiles (the column passes) are swizzled, the one-CTA transforms not
+  auto at = [](int e) { return COLS ? tile_swz(e) : e; };
   typedef typename O::V V;
   constexpr int CNT = (8 + R - 1) / R;
   const int nb = n / R;
@@ -321,14 +333,14 @@ __device__ __forceinline__ void stockham_stage(typename O::V* s, int n, int Ns, 
     int k = j % Ns;
     base[c] = b * bs + ((j - k) * R + k) * is;
     if (act[c] && HALF) {
-      const V* src = s + b * bs + j * is;
+      const int e0 = b * bs + j * is;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) v[c][r] = src[r * nb * is];
+      for (int r = 0; r < 4; ++r) v[c][r] = s[at(e0 + r * nb * is)];
       reg_dft8_half<INV, O>(v[c]);
     } else if (act[c]) {
-      const V* src = s + b * bs + j * is;
+      const int e0 = b * bs + j * is;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[c][r] = src[r * nb * is];
+      for (int r = 0; r < R; ++r) v[c][r] = s[at(e0 + r * nb * is)];
       twiddled_dft<R, INV, O>(v[c], n, Ns, k, twn_n, ft);
     }
   }
@@ -337,7 +349,7 @@ __device__ __forceinline__ void stockham_stage(typename O::V* s, int n, int Ns, 
   for (int c = 0; c < CNT; ++c) {
     if (act[c]) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[base[c] + r * Ns * is] = O::norm(v[c][r]);
+      for (int r = 0; r < R; ++r) s[at(base[c] + r * Ns * is)] = O::norm(v[c][r]);
     }
   }
   __syncthreads();
@@ -392,6 +404,7 @@ struct Tab<OpsF64> {
   static __device__ __forceinline__ const cplx* w(const BlueGeom& g) { return g.w; }
   static __device__ __forceinline__ const cplx* ws(const BlueGeom& g) { return g.ws; }
   static __device__ __forceinline__ const cplx* tw(const BlueGeom& g) { return g.tw; }
+  static __device__ __forceinline__ const cplx* twr(const BlueGeom& g) { return g.twr; }
   static __device__ __forceinline__ const cplx* twn(const BlueGeom& g) { return g.twn; }
   static __device__ __forceinline__ cplx* Bh(const BlueGeom& g) { return g.Bh; }
 };
@@ -400,6 +413,7 @@ struct Tab<OpsDF> {
   static __device__ __forceinline__ const float4* w(const BlueGeom& g) { return g.w_df; }
   static __device__ __forceinline__ const float4* ws(const BlueGeom& g) { return g.ws_df; }
   static __device__ __forceinline__ const float4* tw(const BlueGeom& g) { return g.tw_df; }
+  static __device__ __forceinline__ const float4* twr(const BlueGeom& g) { return g.twr_df; }
   static __device__ __forceinline__ const float4* twn(const BlueGeom& g) { return g.twn_df; }
   static __device__ __forceinline__ float4* Bh(const BlueGeom& g) { return (float4*)g.Bh; }
 };
@@ -568,7 +582,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
         RegDft<8, false, O>::run(out);
       }
 #pragma unroll
-      for (int m = 0; m < 8; ++m) sm[(k1 + m * P1_8) * CB + b] = out[m];
+      for (int m = 0; m < 8; ++m) sm[tile_swz((k1 + m * P1_8) * CB + b)] = out[m];
     }
   };
 
@@ -579,7 +593,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
     for (int e = threadIdx.x; e < rows * CB; e += blockDim.x) {
       int i = e / CB, b = e - i * CB;
       V x = load_input<MODE, O>(g, io, h, M, off, (int64_t)i * P2 + n2_0 + b);
-      sm[e] = x;
+      sm[tile_swz(e)] = x;
       if (O::nonzero(x)) {
         int slot = atomicAdd(&nzc[b], 1);
         if (slot < kColNz) {
@@ -622,14 +636,14 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
       for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
         int k1 = e / CB, b = e - k1 * CB;
         int n2 = n2_0 + b;
-        work[(int64_t)k1 * P2 + n2] = O::mul(sm[e], tw[n2 * k1]);
+        work[(int64_t)k1 * P2 + n2] = O::mul(sm[tile_swz(e)], tw[n2 * k1]);
       }
       return;
     }
   } else {
     for (int e = threadIdx.x; e < rows * CB; e += blockDim.x) {
       int i = e / CB, b = e - i * CB;
-      sm[e] = load_input<MODE, O>(g, io, h, M, off, (int64_t)i * P2 + n2_0 + b);
+      sm[tile_swz(e)] = load_input<MODE, O>(g, io, h, M, off, (int64_t)i * P2 + n2_0 + b);
     }
     __syncthreads();
   }
@@ -645,7 +659,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int k1 = e / CB, b = e - k1 * CB;
     int n2 = n2_0 + b;
-    work[(int64_t)k1 * P2 + n2] = O::mul(sm[e], tw[n2 * k1]);
+    work[(int64_t)k1 * P2 + n2] = O::mul(sm[tile_swz(e)], tw[n2 * k1]);
   }
 }
 
@@ -657,12 +671,15 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
 // last inverse stage, which saves three passes over shared memory and their
 // barriers.
 // ---------------------------------------------------------------------------
+// Shared-memory rows are swizzled like the column tiles (tile_swz).
+__device__ __forceinline__ int row_swz(int i) { return tile_swz(i); }
+
 template <class O>
 struct RowSmem {
   typename O::V* s;
   int P2;
-  __device__ __forceinline__ typename O::V ld(int b, int i) const { return s[b * P2 + i]; }
-  __device__ __forceinline__ void st(int b, int i, typename O::V v) const { s[b * P2 + i] = O::norm(v); }
+  __device__ __forceinline__ typename O::V ld(int b, int i) const { return s[b * P2 + row_swz(i)]; }
+  __device__ __forceinline__ void st(int b, int i, typename O::V v) const { s[b * P2 + row_swz(i)] = O::norm(v); }
 };
 template <class O>
 struct RowLoad {  // the work tile in global memory
@@ -676,16 +693,16 @@ struct RowTimesFilter {  // shared memory <- v * filter spectrum
   const typename O::V* Bh;
   int P2;
   __device__ __forceinline__ void st(int b, int i, typename O::V v) const {
-    s[b * P2 + i] = O::mul(v, Bh[b * P2 + i]);
+    s[b * P2 + row_swz(i)] = O::mul(v, Bh[b * P2 + i]);
   }
 };
 template <class O>
-struct RowStoreTwiddled {  // work tile <- v conj(w_P^(n2 k1))
+struct RowStoreTwiddled {  // work tile <- v conj(w_P^(n2 k1)), twiddles in row order
   typename O::V* p;
-  const typename O::V* tw;
-  int P2, k1_0;
+  const typename O::V* twr;  // rows of the tile: twr[b P2 + n2] = w_P^(n2 (k1_0 + b))
+  int P2;
   __device__ __forceinline__ void st(int b, int i, typename O::V v) const {
-    p[b * P2 + i] = O::mulc(v, tw[i * (k1_0 + b)]);
+    p[b * P2 + i] = O::mulc(v, twr[b * P2 + i]);
   }
 };
 template <class O>
@@ -781,7 +798,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
   }
   row_fft_io<false, O>(sm, P2, RB, Tab<O>::twn(g), src, RowTimesFilter<O>{sm, Bh, P2});
   row_fft_io<true, O>(sm, P2, RB, Tab<O>::twn(g), RowSmem<O>{sm, P2},
-                      RowStoreTwiddled<O>{work, Tab<O>::tw(g), P2, k1_0});
+                      RowStoreTwiddled<O>{work, Tab<O>::twr(g) + (int64_t)k1_0 * P2, P2});
 }
 
 // Pass 3: columns, inverse; natural-order output n = n1 P2 + n2 for n < M.
@@ -799,14 +816,14 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
   const V* work = (const V*)io.work + (int64_t)gi * P;
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int k1 = e / CB, b = e - k1 * CB;
-    sm[e] = work[(int64_t)k1 * P2 + n2_0 + b];
+    sm[tile_swz(e)] = work[(int64_t)k1 * P2 + n2_0 + b];
   }
   __syncthreads();
   smem_fft<true, true, O>(sm, P1, CB, 1, CB, Tab<O>::twn(g));
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int n1 = e / CB, b = e - n1 * CB;
     int64_t n = (int64_t)n1 * P2 + n2_0 + b;
-    if (n < M) store_output<MODE, O>(g, io, h, off, n, sm[e]);
+    if (n < M) store_output<MODE, O>(g, io, h, off, n, sm[tile_swz(e)]);
   }
 }
 
@@ -983,6 +1000,53 @@ const float4* twiddle_table_df(int Pn, cudaStream_t s) {
   to_double_float(src, p, Pn, s);
   MR1L_CUDA(cudaStreamSynchronize(s));
   g_tw_df[key] = p;
+  return p;
+}
+
+template <class T>
+__global__ void row_twiddle_kernel(const T* tw, T* twr, int P2, int64_t P) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= P) return;
+  const int64_t k1 = e / P2, n2 = e - k1 * P2;
+  twr[e] = tw[n2 * k1];  // n2 k1 < P2 P1 = P
+}
+
+namespace {
+std::map<std::pair<int, int>, cplx*> g_twr;     // (device, P) -> row-order table
+std::map<std::pair<int, int>, float4*> g_twr_df;
+}  // namespace
+
+const cplx* row_twiddle_table(int Pn, int P2, cudaStream_t s) {
+  const cplx* src = twiddle_table(Pn, s);
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto key = std::make_pair(dev, Pn);
+  auto it = g_twr.find(key);
+  if (it != g_twr.end()) return it->second;
+  cplx* p = nullptr;
+  MR1L_CUDA(cudaMalloc(&p, (size_t)Pn * sizeof(cplx)));
+  MR1L_LAUNCH("row_twiddle_kernel", s, 0, 32.0 * Pn,
+              row_twiddle_kernel<cplx><<<cdiv(Pn, 256), 256, 0, s>>>(src, p, P2, (int64_t)Pn));
+  MR1L_CUDA(cudaStreamSynchronize(s));
+  g_twr[key] = p;
+  return p;
+}
+
+const float4* row_twiddle_table_df(int Pn, int P2, cudaStream_t s) {
+  const float4* src = twiddle_table_df(Pn, s);
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto key = std::make_pair(dev, Pn);
+  auto it = g_twr_df.find(key);
+  if (it != g_twr_df.end()) return it->second;
+  float4* p = nullptr;
+  MR1L_CUDA(cudaMalloc(&p, (size_t)Pn * sizeof(float4)));
+  MR1L_LAUNCH("row_twiddle_kernel", s, 0, 32.0 * Pn,
+              row_twiddle_kernel<float4><<<cdiv(Pn, 256), 256, 0, s>>>(src, p, P2, (int64_t)Pn));
+  MR1L_CUDA(cudaStreamSynchronize(s));
+  g_twr_df[key] = p;
   return p;
 }
 

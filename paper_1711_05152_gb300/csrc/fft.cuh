@@ -27,6 +27,8 @@ struct BlueGeom {
   const cplx* ws;       // device [sum M]: chirp / M
   cplx* Bh;             // device [L][P]: filter spectrum FFT_P(b) / P (pass order)
   const cplx* tw;       // device [P]: exp(-2 pi i e / P)
+  const cplx* twr;      // device [P1][P2]: exp(-2 pi i n2 k1 / P) at k1 P2 + n2 (the row pass's
+                        //   twiddles in the order it stores them; P > kSmallMax only)
   const cplx* twn;      // device [kSmallTw + kFmaTw]: exp(-2 pi i e / n), n = 2^a <= 8192 at offset n,
                         //   n = 3 * 2^a <= 6144 at offset kSmallTwPow2 + n - 3; then the
                         //   multiply-add twiddles (kFmaTw)
@@ -37,6 +39,7 @@ struct BlueGeom {
   const float4* w_df;
   const float4* ws_df;
   const float4* tw_df;
+  const float4* twr_df;
   const float4* twn_df;
   // complex elements per CTA tile of the column / row passes (set per launch
   // by the tile tuner)
@@ -76,6 +79,11 @@ constexpr int kFmaTw = 7 * kFmaSpan;
 // Device-resident twiddle tables, cached per (device, P).
 const cplx* twiddle_table(int P, cudaStream_t s);
 const float4* twiddle_table_df(int P, cudaStream_t s);
+// The same twiddles in row order for the 4-step split P = P1 x P2 (entry
+// k1 P2 + n2 = exp(-2 pi i n2 k1 / P), copied from twiddle_table), cached per
+// (device, P).
+const cplx* row_twiddle_table(int P, int P2, cudaStream_t s);
+const float4* row_twiddle_table_df(int P, int P2, cudaStream_t s);
 const float4* small_twiddles_df(cudaStream_t s);
 
 // dst[i] = (hi, lo) split of src[i] for i < n (double-float copies of tables).
