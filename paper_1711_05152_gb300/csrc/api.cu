@@ -426,7 +426,10 @@ struct LatticeWork {
     geom.ws = ws.get();
     geom.Bh = Bh.get();
     geom.tw = twiddle_table(P, s);
-    if (P > kSmallMax) geom.twr = row_twiddle_table(P, geom.P2, s);
+    if (P > kSmallMax) {
+      geom.twr = row_twiddle_table(P, geom.P2, s);
+      geom.twc = col_twiddle_table(P, geom.P2, s);
+    }
     geom.twn = small_twiddles(s);
     geom.sum_M = sumM;
     geom.df = df;
@@ -436,7 +439,10 @@ struct LatticeWork {
       geom.w_df = w_df.get();
       geom.ws_df = ws_df.get();
       geom.tw_df = twiddle_table_df(P, s);
-      if (P > kSmallMax) geom.twr_df = row_twiddle_table_df(P, geom.P2, s);
+      if (P > kSmallMax) {
+        geom.twr_df = row_twiddle_table_df(P, geom.P2, s);
+        geom.twc_df = col_twiddle_table_df(P, geom.P2, s);
+      }
       geom.twn_df = small_twiddles_df(s);
     }
     chirp_seed.reserve((size_t)Luse * kChirpSeedLen);

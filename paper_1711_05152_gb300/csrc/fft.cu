@@ -405,6 +405,7 @@ struct Tab<OpsF64> {
   static __device__ __forceinline__ const cplx* ws(const BlueGeom& g) { return g.ws; }
   static __device__ __forceinline__ const cplx* tw(const BlueGeom& g) { return g.tw; }
   static __device__ __forceinline__ const cplx* twr(const BlueGeom& g) { return g.twr; }
+  static __device__ __forceinline__ const cplx* twc(const BlueGeom& g) { return g.twc; }
   static __device__ __forceinline__ const cplx* twn(const BlueGeom& g) { return g.twn; }
   static __device__ __forceinline__ cplx* Bh(const BlueGeom& g) { return g.Bh; }
 };
@@ -414,6 +415,7 @@ struct Tab<OpsDF> {
   static __device__ __forceinline__ const float4* ws(const BlueGeom& g) { return g.ws_df; }
   static __device__ __forceinline__ const float4* tw(const BlueGeom& g) { return g.tw_df; }
   static __device__ __forceinline__ const float4* twr(const BlueGeom& g) { return g.twr_df; }
+  static __device__ __forceinline__ const float4* twc(const BlueGeom& g) { return g.twc_df; }
   static __device__ __forceinline__ const float4* twn(const BlueGeom& g) { return g.twn_df; }
   static __device__ __forceinline__ float4* Bh(const BlueGeom& g) { return (float4*)g.Bh; }
 };
@@ -535,9 +537,9 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
   // RECON / EVAL: rows n1 >= P1/2 hold n >= P/2 >= M, i.e. zero padding
   const int rows = MODE == kModeFilter ? P1 : P1 / 2;
   V* work = (V*)io.work + (int64_t)gi * P;
-  // 4-step twiddle w_P^(n2 k1): n2 < P2 and k1 < P1, so n2 k1 < P indexes the
-  // table without reduction
-  const V* tw = Tab<O>::tw(g);
+  // 4-step twiddle w_P^(n2 k1), in column order (twc[n2 P1 + k1]): the tile's
+  // columns read it contiguously
+  const V* twc = Tab<O>::twc(g) + (int64_t)n2_0 * P1;
   // Evaluation inputs are often sparse (the bins of a few planted
   // frequencies).  A column with at most kColNz non-zeros is transformed
   // directly from its non-zeros, whatever the tiling; the column FFT runs
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
       for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
         int k1 = e / CB, b = e - k1 * CB;
         int n2 = n2_0 + b;
-        work[(int64_t)k1 * P2 + n2] = O::mul(sm[tile_swz(e)], tw[n2 * k1]);
+        work[(int64_t)k1 * P2 + n2] = O::mul(sm[tile_swz(e)], twc[b * P1 + k1]);
       }
       return;
     }
@@ -659,7 +661,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
   for (int e = threadIdx.x; e < P1 * CB; e += blockDim.x) {
     int k1 = e / CB, b = e - k1 * CB;
     int n2 = n2_0 + b;
-    work[(int64_t)k1 * P2 + n2] = O::mul(sm[tile_swz(e)], tw[n2 * k1]);
+    work[(int64_t)k1 * P2 + n2] = O::mul(sm[tile_swz(e)], twc[b * P1 + k1]);
   }
 }
 
@@ -1003,51 +1005,52 @@ const float4* twiddle_table_df(int Pn, cudaStream_t s) {
   return p;
 }
 
-template <class T>
-__global__ void row_twiddle_kernel(const T* tw, T* twr, int P2, int64_t P) {
+// The 4-step twiddles w_P^(n2 k1) (k1 < P1, n2 < P2) copied from the P-point
+// table in row order (entry k1 P2 + n2) or column order (entry n2 P1 + k1).
+template <class T, bool COLS>
+__global__ void ordered_twiddle_kernel(const T* tw, T* out, int P2, int64_t P) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= P) return;
-  const int64_t k1 = e / P2, n2 = e - k1 * P2;
-  twr[e] = tw[n2 * k1];  // n2 k1 < P2 P1 = P
+  const int64_t P1 = P / P2;
+  const int64_t k1 = COLS ? e % P1 : e / P2, n2 = COLS ? e / P1 : e % P2;
+  out[e] = tw[n2 * k1];  // n2 k1 < P2 P1 = P
 }
 
 namespace {
-std::map<std::pair<int, int>, cplx*> g_twr;     // (device, P) -> row-order table
-std::map<std::pair<int, int>, float4*> g_twr_df;
+// (device, P, column order) -> table
+std::map<std::tuple<int, int, int>, cplx*> g_two;
+std::map<std::tuple<int, int, int>, float4*> g_two_df;
+
+template <class T, bool COLS>
+const T* ordered_twiddles(std::map<std::tuple<int, int, int>, T*>& cache, const T* src, int Pn, int P2,
+                          cudaStream_t s) {
+  int dev = 0;
+  MR1L_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto key = std::make_tuple(dev, Pn, COLS ? 1 : 0);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  T* p = nullptr;
+  MR1L_CUDA(cudaMalloc(&p, (size_t)Pn * sizeof(T)));
+  MR1L_LAUNCH("ordered_twiddle_kernel", s, 0, 2.0 * sizeof(T) * Pn,
+              ordered_twiddle_kernel<T, COLS><<<cdiv(Pn, 256), 256, 0, s>>>(src, p, P2, (int64_t)Pn));
+  MR1L_CUDA(cudaStreamSynchronize(s));
+  cache[key] = p;
+  return p;
+}
 }  // namespace
 
 const cplx* row_twiddle_table(int Pn, int P2, cudaStream_t s) {
-  const cplx* src = twiddle_table(Pn, s);
-  int dev = 0;
-  MR1L_CUDA(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(g_tw_mu);
-  auto key = std::make_pair(dev, Pn);
-  auto it = g_twr.find(key);
-  if (it != g_twr.end()) return it->second;
-  cplx* p = nullptr;
-  MR1L_CUDA(cudaMalloc(&p, (size_t)Pn * sizeof(cplx)));
-  MR1L_LAUNCH("row_twiddle_kernel", s, 0, 32.0 * Pn,
-              row_twiddle_kernel<cplx><<<cdiv(Pn, 256), 256, 0, s>>>(src, p, P2, (int64_t)Pn));
-  MR1L_CUDA(cudaStreamSynchronize(s));
-  g_twr[key] = p;
-  return p;
+  return ordered_twiddles<cplx, false>(g_two, twiddle_table(Pn, s), Pn, P2, s);
 }
-
+const cplx* col_twiddle_table(int Pn, int P2, cudaStream_t s) {
+  return ordered_twiddles<cplx, true>(g_two, twiddle_table(Pn, s), Pn, P2, s);
+}
 const float4* row_twiddle_table_df(int Pn, int P2, cudaStream_t s) {
-  const float4* src = twiddle_table_df(Pn, s);
-  int dev = 0;
-  MR1L_CUDA(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(g_tw_mu);
-  auto key = std::make_pair(dev, Pn);
-  auto it = g_twr_df.find(key);
-  if (it != g_twr_df.end()) return it->second;
-  float4* p = nullptr;
-  MR1L_CUDA(cudaMalloc(&p, (size_t)Pn * sizeof(float4)));
-  MR1L_LAUNCH("row_twiddle_kernel", s, 0, 32.0 * Pn,
-              row_twiddle_kernel<float4><<<cdiv(Pn, 256), 256, 0, s>>>(src, p, P2, (int64_t)Pn));
-  MR1L_CUDA(cudaStreamSynchronize(s));
-  g_twr_df[key] = p;
-  return p;
+  return ordered_twiddles<float4, false>(g_two_df, twiddle_table_df(Pn, s), Pn, P2, s);
+}
+const float4* col_twiddle_table_df(int Pn, int P2, cudaStream_t s) {
+  return ordered_twiddles<float4, true>(g_two_df, twiddle_table_df(Pn, s), Pn, P2, s);
 }
 
 const float4* small_twiddles_df(cudaStream_t s) {

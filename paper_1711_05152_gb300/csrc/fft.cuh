@@ -29,6 +29,7 @@ struct BlueGeom {
   const cplx* tw;       // device [P]: exp(-2 pi i e / P)
   const cplx* twr;      // device [P1][P2]: exp(-2 pi i n2 k1 / P) at k1 P2 + n2 (the row pass's
                         //   twiddles in the order it stores them; P > kSmallMax only)
+  const cplx* twc;      // device [P2][P1]: the same twiddles at n2 P1 + k1 (the column pass's order)
   const cplx* twn;      // device [kSmallTw + kFmaTw]: exp(-2 pi i e / n), n = 2^a <= 8192 at offset n,
                         //   n = 3 * 2^a <= 6144 at offset kSmallTwPow2 + n - 3; then the
                         //   multiply-add twiddles (kFmaTw)
@@ -40,6 +41,7 @@ struct BlueGeom {
   const float4* ws_df;
   const float4* tw_df;
   const float4* twr_df;
+  const float4* twc_df;
   const float4* twn_df;
   // complex elements per CTA tile of the column / row passes (set per launch
   // by the tile tuner)
@@ -84,6 +86,9 @@ const float4* twiddle_table_df(int P, cudaStream_t s);
 // (device, P).
 const cplx* row_twiddle_table(int P, int P2, cudaStream_t s);
 const float4* row_twiddle_table_df(int P, int P2, cudaStream_t s);
+// ... and in column order (entry n2 P1 + k1).
+const cplx* col_twiddle_table(int P, int P2, cudaStream_t s);
+const float4* col_twiddle_table_df(int P, int P2, cudaStream_t s);
 const float4* small_twiddles_df(cudaStream_t s);
 
 // dst[i] = (hi, lo) split of src[i] for i < n (double-float copies of tables).
