@@ -1024,7 +1024,12 @@ struct SfftRun {
 
   void noise_setup() {
     if (side) return;
-    MR1L_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    // the noise draws run on the FP32 pipes beside the sampler's FP64
+    // transform; a high priority lets their CTAs take the SM slots that the
+    // transform's CTAs leave free as soon as they are free
+    int lo = 0, hi = 0;
+    MR1L_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    MR1L_CUDA(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi));
     MR1L_CUDA(cudaEventCreateWithFlags(&ev_free, cudaEventDisableTiming));
     MR1L_CUDA(cudaEventCreateWithFlags(&ev_noise, cudaEventDisableTiming));
   }
