@@ -198,10 +198,10 @@ int mr1l_evaluate_batch(mr1l_plan_t* const* plans, int count, const void* const*
  *     L * P) exceeds the fixed maximum of 2^21 complex elements (P is the
  *     plan's Bluestein length, the smallest 2^k or 3 * 2^k >= 2 max M_l - 1).
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.  With CUDA's default lazy module loading,
- *     that first call may also load the library's device code on the device
- *     and commit the array's 32 MiB there; later calls allocate nothing.
+ *     (cudaGetSymbolAddress) with that device current.  With CUDA's default
+ *     lazy module loading, that first call may also load the library's device
+ *     code on the device and commit the array's 32 MiB there; later calls
+ *     allocate nothing.
  *   - Every call shares the one array: calls whose work overlaps on the GPU
  *     (other streams, other host threads) race and must be serialised by the
  *     caller.  No part of the array needs to start at zero.
