@@ -516,10 +516,18 @@ __host__ __device__ __forceinline__ int row_tile(int P2, int P1, int tile) {
 // occupancy; the FP64 passes keep what the compiler picks (up to 128).  The
 // largest lengths (2^25, 3 * 2^23) have single columns of 6144 or rows of
 // 8192 elements, one CTA of up to 1024 threads each (NT = 1024: at most 64
-// registers, so the FP64 kernels spill a little there).
+// registers, so the FP64 kernels spill a little there).  The FP64 inverse
+// column pass over columns of 3072 (P = 3 * 2^21) also has a 384-thread
+// form held to 56 registers, three CTAs per SM instead of two (a few bytes
+// spill): 3 % faster at that length.  The same cap measured slower for the
+// forward column pass and in double-float.
 template <class O>
 struct MinBlocks {
   static constexpr int value = std::is_same<O, OpsDF>::value ? 2 : 1;
+};
+template <class O, int NT>
+struct ColBlocks {
+  static constexpr int value = NT == 512 ? MinBlocks<O>::value : NT == 384 ? 3 : 1;
 };
 
 // Pass 1: columns, forward, with the 4-step twiddle.
@@ -805,7 +813,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
 
 // Pass 3: columns, inverse; natural-order output n = n1 P2 + n2 for n < M.
 template <int MODE, class O, int NT = 512>
-__global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
+__global__ void __launch_bounds__(NT, (ColBlocks<O, NT>::value)) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -1131,6 +1139,24 @@ static const char* pass_name(const char* pass, std::string& nm) {
   return nm.c_str();
 }
 
+// The FP64 inverse column pass in its 384-thread, three-CTA form (columns of
+// 3072); false where that form does not exist.
+template <int MODE, class O>
+static bool col_inv_384(const BlueGeom& g, const BlueIO& io, dim3 gc, size_t smem_c, double flops, double bytes,
+                        cudaStream_t s) {
+  if constexpr (std::is_same<O, OpsF64>::value && MODE != kModeFilter) {
+    auto k = blue_col_inv_kernel<MODE, O, 384>;
+    set_smem(k, smem_c);
+    // room for three CTAs of 48 KB dynamic and up to 7 KB static shared memory
+    MR1L_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared));
+    std::string nm;
+    MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s, flops, bytes, k<<<gc, 384, smem_c, s>>>(g, io));
+    return true;
+  }
+  return false;
+}
+
 // The 4-step passes with the tiles in g.ctile / g.rtile.  ev (optional):
 // events recorded before the column pass and after each pass.
 template <int MODE, class O>
@@ -1187,9 +1213,11 @@ static void launch_passes(const BlueGeom& g, const BlueIO& io, int ntrans, cudaS
   const double fl_ci = ntrans * P2 * fft_flops(P1) + (MODE == kModeEval ? nr * 6 * sumM : 0.0);
   const double by_ci = ntrans * P * cb + nr * sumM * cb * (MODE == kModeEval ? 2 : 1);
   if (tc <= 512) {
-    set_smem(blue_col_inv_kernel<MODE, O>, smem_c);
-    MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s, fl_ci, by_ci,
-                blue_col_inv_kernel<MODE, O><<<gc, tc, smem_c, s>>>(g, io));
+    if (!(tc == 384 && col_inv_384<MODE, O>(g, io, gc, smem_c, fl_ci, by_ci, s))) {
+      set_smem(blue_col_inv_kernel<MODE, O>, smem_c);
+      MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s, fl_ci, by_ci,
+                  blue_col_inv_kernel<MODE, O><<<gc, tc, smem_c, s>>>(g, io));
+    }
   } else {
     set_smem(blue_col_inv_kernel<MODE, O, 1024>, smem_c);
     MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s, fl_ci, by_ci,
