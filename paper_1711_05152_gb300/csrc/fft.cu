@@ -472,16 +472,16 @@ __global__ void __launch_bounds__(512) blue_small_kernel(BlueGeom g, BlueIO io) 
   else
     smem_fft<false, false, O>(sm, P, 1, 0, 1, Tab<O>::twn(g));
   V* Bh = Tab<O>::Bh(g) + (int64_t)l * P;
-  if (MODE == kModeFilter) {
+  if constexpr (MODE == kModeFilter) {
     const double sc = 1.0 / (double)P;
     const float sh = __double2float_rn(sc), sl = __double2float_rn(sc - (double)sh);
     for (int n = threadIdx.x; n < P; n += blockDim.x) Bh[n] = O::scalec(sm[n], sc, sh, sl);
-    return;
+  } else {
+    for (int n = threadIdx.x; n < P; n += blockDim.x) sm[n] = O::mul(sm[n], Bh[n]);
+    __syncthreads();
+    smem_fft<true, false, O>(sm, P, 1, 0, 1, Tab<O>::twn(g));
+    for (int n = threadIdx.x; n < M; n += blockDim.x) store_output<MODE, O>(g, io, h, off, n, sm[n]);
   }
-  for (int n = threadIdx.x; n < P; n += blockDim.x) sm[n] = O::mul(sm[n], Bh[n]);
-  __syncthreads();
-  smem_fft<true, false, O>(sm, P, 1, 0, 1, Tab<O>::twn(g));
-  for (int n = threadIdx.x; n < M; n += blockDim.x) store_output<MODE, O>(g, io, h, off, n, sm[n]);
 }
 
 // ---------------------------------------------------------------------------
@@ -513,26 +513,39 @@ __host__ __device__ __forceinline__ int row_tile(int P2, int P1, int tile) {
 // Register budget of the 4-step kernels: the double-float passes wait on
 // memory more than on arithmetic, so they are held to 64 registers (two
 // 512-thread or four 256-thread CTAs per SM; a few bytes spill) for the
-// occupancy; the FP64 passes keep what the compiler picks (up to 128).  The
-// largest lengths (2^25, 3 * 2^23) have single columns of 6144 or rows of
+// occupancy; the FP64 column passes otherwise keep what the compiler picks
+// (up to 128).  The largest lengths (2^25, 3 * 2^23) have single columns of 6144 or rows of
 // 8192 elements, one CTA of up to 1024 threads each (NT = 1024: at most 64
-// registers, so the FP64 kernels spill a little there).  The FP64 inverse
-// column pass over columns of 3072 (P = 3 * 2^21) also has a 384-thread
-// form held to 56 registers, three CTAs per SM instead of two (a few bytes
-// spill): 3 % faster at that length.  The same cap measured slower for the
-// forward column pass and in double-float.
+// registers, so the FP64 kernels spill a little there).
+// At P = 3 * 2^21 (columns of 3072 in CTAs of 384 threads, rows of 2048 in
+// CTAs of 256) the FP64 passes have register-capped forms that fit one more
+// CTA per SM: the evaluation column pass 80 registers (two CTAs instead of
+// one, -29 %), the row pass 80 (three instead of two, -1.5 %), the inverse
+// column pass 56 (three instead of two, 16 bytes spill, -3 %).  The same cap
+// measured slower for the reconstruct column pass (its chirp products need
+// the registers) and in double-float (more spills).  FP64 rows in CTAs of 512
+// threads (rows of 4096 at P = 2^23) are held to 64 registers, two CTAs per
+// SM instead of one, with no spill.
 template <class O>
 struct MinBlocks {
   static constexpr int value = std::is_same<O, OpsDF>::value ? 2 : 1;
 };
 template <class O, int NT>
-struct ColBlocks {
+struct ColFwdBlocks {
+  static constexpr int value = NT == 512 ? MinBlocks<O>::value : NT == 384 ? 2 : 1;
+};
+template <class O, int NT>
+struct RowBlocks {
+  static constexpr int value = NT == 512 ? 2 : NT == 256 ? 3 : 1;
+};
+template <class O, int NT>
+struct ColInvBlocks {
   static constexpr int value = NT == 512 ? MinBlocks<O>::value : NT == 384 ? 3 : 1;
 };
 
 // Pass 1: columns, forward, with the 4-step twiddle.
 template <int MODE, class O, int NT = 512>
-__global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_col_fwd_kernel(BlueGeom g, BlueIO io) {
+__global__ void __launch_bounds__(NT, (ColFwdBlocks<O, NT>::value)) blue_col_fwd_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -789,7 +802,7 @@ __device__ __forceinline__ void row_fft_io(typename O::V* sm, int P2, int nrows,
 // FFT, times Bh, inverse FFT, times conj(w_P^(n2 k1)), with the loads and
 // stores fused into the first and last stages (row_fft_io).
 template <bool FILTER, class O, int NT = 512>
-__global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_row_kernel(BlueGeom g, BlueIO io) {
+__global__ void __launch_bounds__(NT, (RowBlocks<O, NT>::value)) blue_row_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -813,7 +826,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? MinBlocks<O>::value : 1) blue_
 
 // Pass 3: columns, inverse; natural-order output n = n1 P2 + n2 for n < M.
 template <int MODE, class O, int NT = 512>
-__global__ void __launch_bounds__(NT, (ColBlocks<O, NT>::value)) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
+__global__ void __launch_bounds__(NT, (ColInvBlocks<O, NT>::value)) blue_col_inv_kernel(BlueGeom g, BlueIO io) {
   typedef typename O::V V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = (V*)smraw;
@@ -1139,28 +1152,28 @@ static const char* pass_name(const char* pass, std::string& nm) {
   return nm.c_str();
 }
 
-// The FP64 inverse column pass in its 384-thread, three-CTA form (columns of
-// 3072); false where that form does not exist.
-template <int MODE, class O>
-static bool col_inv_384(const BlueGeom& g, const BlueIO& io, dim3 gc, size_t smem_c, double flops, double bytes,
-                        cudaStream_t s) {
-  if constexpr (std::is_same<O, OpsF64>::value && MODE != kModeFilter) {
-    auto k = blue_col_inv_kernel<MODE, O, 384>;
-    set_smem(k, smem_c);
-    // room for three CTAs of 48 KB dynamic and up to 7 KB static shared memory
-    MR1L_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+// One pass: the dynamic shared-memory size set on the kernel (and, for forms
+// that need room for three CTAs, the largest shared-memory carveout), then
+// the launch under its profiling name.
+template <typename K>
+static void run_pass(K kern, const char* name, dim3 grid, int threads, size_t smem, bool carveout, double flops,
+                     double bytes, const BlueGeom& g, const BlueIO& io, cudaStream_t s) {
+  set_smem(kern, smem);
+  if (carveout)
+    MR1L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                    (int)cudaSharedmemCarveoutMaxShared));
-    std::string nm;
-    MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s, flops, bytes, k<<<gc, 384, smem_c, s>>>(g, io));
-    return true;
-  }
-  return false;
+  MR1L_LAUNCH(name, s, flops, bytes, kern<<<grid, threads, smem, s>>>(g, io));
 }
 
 // The 4-step passes with the tiles in g.ctile / g.rtile.  ev (optional):
-// events recorded before the column pass and after each pass.
+// events recorded before the column pass and after each pass.  The FP64
+// passes at the block sizes of P = 3 * 2^21 (columns of 3072: 384 threads;
+// rows of 2048: 256 threads) use their register-capped forms.
 template <int MODE, class O>
 static void launch_passes(const BlueGeom& g, const BlueIO& io, int ntrans, cudaStream_t s, cudaEvent_t* ev) {
+  constexpr bool f64 = std::is_same<O, OpsF64>::value;
+  constexpr int kCf = f64 && MODE == kModeEval ? 384 : 512, kR = f64 ? 256 : 512,
+                kCi = f64 && MODE != kModeFilter ? 384 : 512;
   const double P = g.P, nr = (double)ntrans / g.L, sumM = (double)g.sum_M;
   const double cb = sizeof(cplx);
   std::string nm;
@@ -1173,56 +1186,49 @@ static void launch_passes(const BlueGeom& g, const BlueIO& io, int ntrans, cudaS
   const int tc = threads_for(g.P1 * CB), tr = threads_for(RB * g.P2);
   MR1L_REQUIRE(tc <= 1024 && tr <= 1024, "4-step tile larger than one CTA");
   if (ev) MR1L_CUDA(cudaEventRecord(ev[0], s));
-  if (tc <= 512) {
-    set_smem(blue_col_fwd_kernel<MODE, O>, smem_c);
-    MR1L_LAUNCH((pass_name<MODE, O>("col_fwd", nm)), s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM,
-                nr * sumM * cb * 2 + ntrans * P * cb, blue_col_fwd_kernel<MODE, O><<<gc, tc, smem_c, s>>>(g, io));
-  } else {
-    set_smem(blue_col_fwd_kernel<MODE, O, 1024>, smem_c);
-    MR1L_LAUNCH((pass_name<MODE, O>("col_fwd", nm)), s, ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM,
-                nr * sumM * cb * 2 + ntrans * P * cb,
-                blue_col_fwd_kernel<MODE, O, 1024><<<gc, tc, smem_c, s>>>(g, io));
-  }
+
+  const char* name = pass_name<MODE, O>("col_fwd", nm);
+  const double fl_cf = ntrans * (P2 * fft_flops(P1) + 6 * P) + nr * 6 * sumM;
+  const double by_cf = nr * sumM * cb * 2 + ntrans * P * cb;
+  if (kCf == 384 && tc == 384)
+    run_pass(blue_col_fwd_kernel<MODE, O, kCf>, name, gc, tc, smem_c, false, fl_cf, by_cf, g, io, s);
+  else if (tc <= 512)
+    run_pass(blue_col_fwd_kernel<MODE, O>, name, gc, tc, smem_c, false, fl_cf, by_cf, g, io, s);
+  else
+    run_pass(blue_col_fwd_kernel<MODE, O, 1024>, name, gc, tc, smem_c, false, fl_cf, by_cf, g, io, s);
   if (ev) MR1L_CUDA(cudaEventRecord(ev[1], s));
+
+  name = pass_name<MODE, O>("row", nm);
   if (MODE == kModeFilter) {
-    if (tr <= 512) {
-      set_smem(blue_row_kernel<true, O>, smem_r);
-      MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
-                  blue_row_kernel<true, O><<<gr, tr, smem_r, s>>>(g, io));
-    } else {
-      set_smem(blue_row_kernel<true, O, 1024>, smem_r);
-      MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * P1 * fft_flops(P2), ntrans * P * cb * 2,
-                  blue_row_kernel<true, O, 1024><<<gr, tr, smem_r, s>>>(g, io));
-    }
+    const double fl = ntrans * P1 * fft_flops(P2), by = ntrans * P * cb * 2;
+    if (tr <= 512)
+      run_pass(blue_row_kernel<true, O>, name, gr, tr, smem_r, false, fl, by, g, io, s);
+    else
+      run_pass(blue_row_kernel<true, O, 1024>, name, gr, tr, smem_r, false, fl, by, g, io, s);
     if (ev) {
       MR1L_CUDA(cudaEventRecord(ev[2], s));
       MR1L_CUDA(cudaEventRecord(ev[3], s));
     }
     return;
   }
-  if (tr <= 512) {
-    set_smem(blue_row_kernel<false, O>, smem_r);
-    MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
-                blue_row_kernel<false, O><<<gr, tr, smem_r, s>>>(g, io));
-  } else {
-    set_smem(blue_row_kernel<false, O, 1024>, smem_r);
-    MR1L_LAUNCH((pass_name<MODE, O>("row", nm)), s, ntrans * (2 * P1 * fft_flops(P2) + 12 * P), ntrans * P * cb * 3,
-                blue_row_kernel<false, O, 1024><<<gr, tr, smem_r, s>>>(g, io));
-  }
+  const double fl_r = ntrans * (2 * P1 * fft_flops(P2) + 12 * P), by_r = ntrans * P * cb * 3;
+  if (kR == 256 && tr == 256)
+    run_pass(blue_row_kernel<false, O, kR>, name, gr, tr, smem_r, false, fl_r, by_r, g, io, s);
+  else if (tr <= 512)
+    run_pass(blue_row_kernel<false, O>, name, gr, tr, smem_r, false, fl_r, by_r, g, io, s);
+  else
+    run_pass(blue_row_kernel<false, O, 1024>, name, gr, tr, smem_r, false, fl_r, by_r, g, io, s);
   if (ev) MR1L_CUDA(cudaEventRecord(ev[2], s));
+
+  name = pass_name<MODE, O>("col_inv", nm);
   const double fl_ci = ntrans * P2 * fft_flops(P1) + (MODE == kModeEval ? nr * 6 * sumM : 0.0);
   const double by_ci = ntrans * P * cb + nr * sumM * cb * (MODE == kModeEval ? 2 : 1);
-  if (tc <= 512) {
-    if (!(tc == 384 && col_inv_384<MODE, O>(g, io, gc, smem_c, fl_ci, by_ci, s))) {
-      set_smem(blue_col_inv_kernel<MODE, O>, smem_c);
-      MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s, fl_ci, by_ci,
-                  blue_col_inv_kernel<MODE, O><<<gc, tc, smem_c, s>>>(g, io));
-    }
-  } else {
-    set_smem(blue_col_inv_kernel<MODE, O, 1024>, smem_c);
-    MR1L_LAUNCH((pass_name<MODE, O>("col_inv", nm)), s, fl_ci, by_ci,
-                blue_col_inv_kernel<MODE, O, 1024><<<gc, tc, smem_c, s>>>(g, io));
-  }
+  if (kCi == 384 && tc == 384)  // three CTAs of 48 KB dynamic and up to 7 KB static shared memory
+    run_pass(blue_col_inv_kernel<MODE, O, kCi>, name, gc, tc, smem_c, true, fl_ci, by_ci, g, io, s);
+  else if (tc <= 512)
+    run_pass(blue_col_inv_kernel<MODE, O>, name, gc, tc, smem_c, false, fl_ci, by_ci, g, io, s);
+  else
+    run_pass(blue_col_inv_kernel<MODE, O, 1024>, name, gc, tc, smem_c, false, fl_ci, by_ci, g, io, s);
   if (ev) MR1L_CUDA(cudaEventRecord(ev[3], s));
 }
 
