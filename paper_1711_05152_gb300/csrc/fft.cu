@@ -518,14 +518,15 @@ __host__ __device__ __forceinline__ int row_tile(int P2, int P1, int tile) {
 // 8192 elements, one CTA of up to 1024 threads each (NT = 1024: at most 64
 // registers, so the FP64 kernels spill a little there).
 // At P = 3 * 2^21 (columns of 3072 in CTAs of 384 threads, rows of 2048 in
-// CTAs of 256) the FP64 passes have register-capped forms that fit one more
-// CTA per SM: the evaluation column pass 80 registers (two CTAs instead of
-// one, -29 %), the row pass 80 (three instead of two, -1.5 %), the inverse
-// column pass 56 (three instead of two, 16 bytes spill, -3 %).  The same cap
-// measured slower for the reconstruct column pass (its chirp products need
-// the registers) and in double-float (more spills).  FP64 rows in CTAs of 512
-// threads (rows of 4096 at P = 2^23) are held to 64 registers, two CTAs per
-// SM instead of one, with no spill.
+// CTAs of 256 or, two rows each, 512) the FP64 passes have register-capped
+// forms that fit one more CTA per SM: the evaluation column pass 80
+// registers (two CTAs instead of one, -29 %), the rows 80 in CTAs of 256
+// (three instead of two) and 64 in CTAs of 512 (two instead of one; also
+// the rows of 4096 at P = 2^23), the inverse column pass 56 (three instead
+// of two, 16 bytes spill, -3 %).  With the caps the tile tuner picks two
+// rows per CTA at that length (rows -2 %).  The same cap measured slower for
+// the reconstruct column pass (its chirp products need the registers) and in
+// double-float (more spills).
 template <class O>
 struct MinBlocks {
   static constexpr int value = std::is_same<O, OpsDF>::value ? 2 : 1;
@@ -1168,7 +1169,8 @@ static void run_pass(K kern, const char* name, dim3 grid, int threads, size_t sm
 // The 4-step passes with the tiles in g.ctile / g.rtile.  ev (optional):
 // events recorded before the column pass and after each pass.  The FP64
 // passes at the block sizes of P = 3 * 2^21 (columns of 3072: 384 threads;
-// rows of 2048: 256 threads) use their register-capped forms.
+// one row of 2048: 256 threads) use their register-capped forms, as do all
+// FP64 rows in CTAs of 512 threads.
 template <int MODE, class O>
 static void launch_passes(const BlueGeom& g, const BlueIO& io, int ntrans, cudaStream_t s, cudaEvent_t* ev) {
   constexpr bool f64 = std::is_same<O, OpsF64>::value;
