@@ -964,6 +964,9 @@ static void stage_h2d(Staging* st, void* dst, const void* src, size_t bytes, cud
     MR1L_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
 }
 
+// Largest FFT work array of one group of fused repetitions (32 GiB).
+constexpr int64_t kRepGroupBytes = int64_t(1) << 35;
+
 struct SfftRun {
   sfft_params P;
   sfft_sampler S;
@@ -1301,7 +1304,14 @@ struct SfftRun {
       MR1L_CUDA(cudaMemsetAsync(flags.get(), 0, n, s));
       // steps 2c-2e
       if (P.batch_reps) {
-        passes(J, t, 0, rt, cap);
+        // the repetitions in groups: a launch covers the Luse lattices of each
+        // repetition of its group (grid.y = Luse x repetitions <= 65535), and
+        // a group's FFT work array stays within kRepGroupBytes (one group for
+        // the usual r <= 10)
+        const int64_t per_rep = (int64_t)Luse * lw.geom.P * (int64_t)sizeof(cplx);
+        const int group = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)rt, 65535 / Luse,
+                                                                        kRepGroupBytes / per_rep}));
+        for (int i = 0; i < rt; i += group) passes(J, t, i, std::min(group, rt - i), cap);
       } else {
         for (int i = 0; i < rt; ++i) passes(J, t, i, 1, cap);
       }
