@@ -559,6 +559,11 @@ struct mr1l_plan_s {
   LatticeWork lw;
   // grow-only transform scratch
   DevBuf<cplx> C, bins, work;
+  // the adjoint's bin -> candidate map and per-candidate 1 / cnt, built once
+  DevBuf<int32_t> adj_map;
+  DevBuf<double> adj_inv;
+  DevBuf<cplx> adj_coef;  // scratch: the coefficients scaled by 1 / cnt_k
+  bool adj_ready = false;
   CandSet cand() const {
     CandSet J;
     J.tp = t;
@@ -743,15 +748,33 @@ static void evaluate_impl(mr1l_plan_t* plan, const void* c, int nrhs, void* y, i
   const int64_t sumM = lw.sumM;
   plan->bins.reserve((size_t)nrhs * sumM);
   plan->work.reserve((size_t)nrhs * lw.Luse * lw.geom.P);
-  MR1L_CUDA(cudaMemsetAsync(plan->bins.get(), 0, (size_t)nrhs * sumM * sizeof(cplx), s));
-  scatter(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, (const cplx*)c, plan->nI, nrhs,
-          mode == MR1L_ADJOINT, plan->bins.get(), sumM, lw.pairs(), s);
+  if (mode == MR1L_ADJOINT) {
+    // the bin -> candidate map of the adjoint, built on the first adjoint
+    // transform of the plan
+    if (!plan->adj_ready) {
+      plan->adj_map.reserve(sumM);
+      plan->adj_inv.reserve(plan->nI);
+      MR1L_CUDA(cudaMemsetAsync(plan->adj_map.get(), 0xff, sumM * sizeof(int32_t), s));
+      adjoint_map(plan->cand(), lw.dev(), lw.Luse, lw.umask.get(), lw.geom, plan->adj_map.get(),
+                  plan->adj_inv.get(), lw.pairs(), s);
+      plan->adj_ready = true;
+    }
+    int maxM = 0;
+    for (int l = 0; l < lw.Luse; ++l) maxM = std::max(maxM, lw.Mh[l]);
+    plan->adj_coef.reserve((size_t)nrhs * plan->nI);
+    adjoint_bins(lw.Luse, maxM, lw.geom, plan->nI, plan->adj_map.get(), plan->adj_inv.get(), (const cplx*)c,
+                 plan->nI, nrhs, plan->adj_coef.get(), plan->bins.get(), sumM, s);
+  } else {
+    MR1L_CUDA(cudaMemsetAsync(plan->bins.get(), 0, (size_t)nrhs * sumM * sizeof(cplx), s));
+    scatter(plan->cand(), lw.dev(), lw.Luse, lw.geom, (const cplx*)c, plan->nI, nrhs, plan->bins.get(), sumM, s);
+  }
   BlueIO io{};
   io.in = plan->bins.get();
   io.in_stride = sumM;
   io.out = (cplx*)y;
   io.out_stride = sumM;
   io.work = plan->work.get();
+  io.out_scaled = mode == MR1L_ADJOINT;
   blue_run(lw.geom, io, kModeEval, nrhs, s);
 }
 

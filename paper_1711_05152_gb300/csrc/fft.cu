@@ -443,10 +443,12 @@ __device__ __forceinline__ typename O::V load_input(const BlueGeom& g, const Blu
 template <int MODE, class O>
 __device__ __forceinline__ void store_output(const BlueGeom& g, const BlueIO& io, int h, int64_t off, int64_t n,
                                              typename O::V v) {
-  if (MODE == kModeRecon)
+  if (MODE == kModeRecon) {
     io.out[h * io.out_stride + off + n] = O::to(v);
-  else
-    io.out[h * io.out_stride + off + n] = O::to(O::conj(O::mul(Tab<O>::w(g)[off + n], v)));
+  } else {
+    const typename O::V* wt = io.out_scaled ? Tab<O>::ws(g) : Tab<O>::w(g);
+    io.out[h * io.out_stride + off + n] = O::to(O::conj(O::mul(wt[off + n], v)));
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -64,6 +64,7 @@ struct BlueIO {
   int noise_t, noise_rep;
   int noise_rep_per_rhs;  // rep index = noise_rep + rhs * noise_rep_per_rhs
   int no_tune;            // 1: never run tiling trials (default tiles unless already tuned)
+  int out_scaled;         // EVAL: output chirp divided by M_l (the 1 / M_l of the adjoint)
 };
 
 constexpr int kSmallMax = 4096;  // P <= 4096: one CTA holds the whole transform

@@ -235,56 +235,113 @@ void gather(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* u
 }
 
 // ---------------------------------------------------------------------------
-// Scatter into lattice bins (evaluation: all lattices, weight c_k; adjoint:
-// lattices with c in I_l, weight c_k / (cnt_k M_l)).
+// Scatter into lattice bins for evaluation: all lattices, weight c_k; a bin
+// that several candidates share (a collision) sums them, hence the atomics.
 // ---------------------------------------------------------------------------
-__global__ void scatter_kernel(CandSet J, LatticeDev lat, uint64_t lmask, const uint64_t* umask,
-                               const int64_t* off, const cplx* coef, int64_t coef_stride, int adjoint,
-                               cplx* bins, int64_t bins_stride) {
+__global__ void scatter_kernel(CandSet J, LatticeDev lat, uint64_t lmask, const int64_t* off, const cplx* coef,
+                               int64_t coef_stride, cplx* bins, int64_t bins_stride) {
   const int h = blockIdx.y;
   const int64_t n = J.np * J.nq;
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= n) return;
   int64_t p = c / J.nq, q = c - p * J.nq;
-  cplx v = coef[h * coef_stride + c];
+  const cplx v = coef[h * coef_stride + c];
   uint64_t m = lmask;
-  double inv_cnt = 1.0;
-  if (adjoint) {
-    m &= umask[c];
-    int cnt = __popcll(m);
-    if (!cnt) return;
-    inv_cnt = __drcp_rn((double)cnt);
-  }
   cplx* B = bins + h * bins_stride;
   while (m) {
     int l = __ffsll((long long)m) - 1;
     m &= m - 1;
-    uint32_t M = (uint32_t)lat.M[l];
-    uint32_t r = residue_of(lat, J.np, J.nq, l, p, q, M);
-    cplx u = v;
-    if (adjoint) {
-      double sc = inv_cnt * __drcp_rn((double)M);
-      u = cmake(v.x * sc, v.y * sc);
-    }
+    uint32_t r = residue_of(lat, J.np, J.nq, l, p, q, (uint32_t)lat.M[l]);
     double* dst = (double*)(B + off[l] + r);
-    atomicAdd(dst, u.x);
-    atomicAdd(dst + 1, u.y);
+    atomicAdd(dst, v.x);
+    atomicAdd(dst + 1, v.y);
   }
 }
 
-void scatter(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
-             const cplx* coef, int64_t coef_stride, int nrhs, int adjoint, cplx* bins, int64_t bins_stride,
-             int64_t pairs, cudaStream_t s) {
+void scatter(const CandSet& J, const LatticeDev& lat, int Luse, const BlueGeom& g, const cplx* coef,
+             int64_t coef_stride, int nrhs, cplx* bins, int64_t bins_stride, cudaStream_t s) {
   const int64_t n = J.n();
   if (n == 0 || nrhs == 0) return;
   uint64_t lmask = Luse >= 64 ? ~0ull : ((1ull << Luse) - 1);
-  // algorithmic bytes: the coefficients (and masks) in, one complex
-  // read-modify-write per (k, l) pair (all lattices for EVAL, k in I_l for ADJOINT)
-  const double bytes = (double)nrhs * (16.0 * n + 32.0 * (adjoint ? pairs : n * (int64_t)Luse)) +
-                       (adjoint ? 8.0 * n : 0.0);
+  // algorithmic bytes: the coefficients in, one complex read-modify-write per
+  // (k, l) pair
+  const double bytes = (double)nrhs * (16.0 * n + 32.0 * n * (int64_t)Luse);
   MR1L_LAUNCH("scatter_kernel", s, 0, bytes,
-              scatter_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, umask, g.off, coef, coef_stride,
-                                                                       adjoint, bins, bins_stride));
+              scatter_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(J, lat, lmask, g.off, coef, coef_stride, bins,
+                                                                       bins_stride));
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of Algorithm 2 in bin order.  A candidate's coefficient reaches only
+// the bins where it is collision-free, and such a bin belongs to that
+// candidate alone, so the adjoint is a map from bins to candidates, built once
+// per plan (random 4-byte stores).  A transform then scales the coefficients
+// by 1 / cnt_k (one dense pass; the 1 / M_l goes into the output chirp of the
+// evaluation pass) and writes every bin once, in order, copying its
+// candidate's value (a small array that stays in L2): no FP64 instruction in
+// the sparse pass, which on this GPU costs a whole warp's issue even with few
+// lanes active, and no random read-modify-write of 32-byte sectors.
+// ---------------------------------------------------------------------------
+__global__ void adjoint_map_kernel(CandSet J, LatticeDev lat, uint64_t lmask, const uint64_t* umask,
+                                   const int64_t* off, int32_t* map, double* inv_cnt) {
+  const int64_t n = J.np * J.nq;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int64_t p = c / J.nq, q = c - p * J.nq;
+  uint64_t m = umask[c] & lmask;
+  const int cnt = __popcll(m);
+  inv_cnt[c] = cnt ? __drcp_rn((double)cnt) : 0.0;
+  while (m) {
+    const int l = __ffsll((long long)m) - 1;
+    m &= m - 1;
+    map[off[l] + residue_of(lat, J.np, J.nq, l, p, q, (uint32_t)lat.M[l])] = (int32_t)c;
+  }
+}
+
+void adjoint_map(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
+                 int32_t* map, double* inv_cnt, int64_t pairs, cudaStream_t s) {
+  const int64_t n = J.n();
+  if (n == 0) return;
+  MR1L_REQUIRE(n < (int64_t(1) << 31), "too many candidates for the adjoint map");
+  uint64_t lmask = Luse >= 64 ? ~0ull : ((1ull << Luse) - 1);
+  MR1L_LAUNCH("adjoint_map_kernel", s, 0, 16.0 * n + 4.0 * pairs,
+              adjoint_map_kernel<<<cdiv(n, 256), 256, 0, s>>>(J, lat, lmask, umask, g.off, map, inv_cnt));
+}
+
+__global__ void adjoint_scale_kernel(const cplx* coef, int64_t coef_stride, int64_t n, const double* inv_cnt,
+                                     cplx* cs) {
+  const int h = blockIdx.y;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const cplx v = coef[h * coef_stride + c];
+  const double sc = inv_cnt[c];
+  cs[h * n + c] = cmake(v.x * sc, v.y * sc);
+}
+
+// grid (bins of the largest lattice / 256, lattices, right-hand sides)
+__global__ void adjoint_bins_kernel(const int* M, const int64_t* off, const int32_t* map, const cplx* cs, int64_t n,
+                                    cplx* bins, int64_t bins_stride) {
+  const int l = blockIdx.y, h = blockIdx.z;
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= M[l]) return;
+  const int64_t b = off[l] + j;
+  const int32_t c = map[b];
+  bins[h * bins_stride + b] = c >= 0 ? cs[h * n + c] : cmake(0.0, 0.0);
+}
+
+void adjoint_bins(int Luse, int maxM, const BlueGeom& g, int64_t n, const int32_t* map, const double* inv_cnt,
+                  const cplx* coef, int64_t coef_stride, int nrhs, cplx* cs, cplx* bins, int64_t bins_stride,
+                  cudaStream_t s) {
+  if (nrhs == 0 || Luse == 0) return;
+  if (n > 0)
+    MR1L_LAUNCH("adjoint_scale_kernel", s, 0, 32.0 * nrhs * n + 8.0 * n,
+                adjoint_scale_kernel<<<dim3(cdiv(n, 256), nrhs), 256, 0, s>>>(coef, coef_stride, n, inv_cnt, cs));
+  // algorithmic bytes: every bin written once, the map and the scaled
+  // coefficients read once
+  const double bytes = 16.0 * nrhs * (double)g.sum_M + 4.0 * (double)g.sum_M + 16.0 * nrhs * (double)n;
+  MR1L_LAUNCH("adjoint_bins_kernel", s, 0, bytes,
+              adjoint_bins_kernel<<<dim3(cdiv(maxM, 256), Luse, nrhs), 256, 0, s>>>(g.M, g.off, map, cs, n, bins,
+                                                                                    bins_stride));
 }
 
 // ---------------------------------------------------------------------------

@@ -1,6 +1,6 @@
 // Lattice-side kernels of the hot path: residues, collision counting and
 // coverage (Algorithm 1 / condition 2.1), the averaged gather (Algorithm 2),
-// scatter into lattice bins (evaluation and adjoint), the planted sampler,
+// the lattice bins of evaluation and adjoint, the planted sampler,
 // 1-D line detection (steps 1 and 2a of Algorithm 3), thresholded top-s
 // selection and compaction.
 #pragma once
@@ -52,11 +52,24 @@ void gather(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* u
             const cplx* C, int64_t C_stride, int nrhs, cplx* p, int64_t p_stride, uint64_t* keys,
             uint64_t* keymax, int64_t pairs, cudaStream_t s);
 
-// Scatter for evaluation: bins[h][off_l + r_l(c)] += weight, with weight c_k
-// (ADJOINT: c_k / (cnt_k M_l) for c in I_l only).  bins must be zeroed.
-void scatter(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
-             const cplx* coef, int64_t coef_stride, int nrhs, int adjoint, cplx* bins, int64_t bins_stride,
-             int64_t pairs, cudaStream_t s);
+// Scatter for evaluation (EVAL): bins[h][off_l + r_l(c)] += c_k over all
+// lattices l < Luse (colliding candidates share a bin).  bins must be zeroed.
+void scatter(const CandSet& J, const LatticeDev& lat, int Luse, const BlueGeom& g, const cplx* coef,
+             int64_t coef_stride, int nrhs, cplx* bins, int64_t bins_stride, cudaStream_t s);
+
+// The adjoint of Algorithm 2 (ADJOINT) in bin order.  adjoint_map (once per
+// plan): map[off_l + r] = the candidate collision-free at residue r of
+// lattice l (at most one: that is what collision-free means), -1 where there
+// is none; inv_cnt[c] = 1 / |{l < Luse : c in I_l}| (0 if uncovered).  map
+// must hold -1 everywhere beforehand.  adjoint_bins: cs[h][c] = c_k / cnt_k
+// (scratch [nrhs][n]), then every bin bins[h][off_l + j] = cs[h][k] for the
+// candidate k of map, else 0 (maxM: the largest M_l, l < Luse); the 1 / M_l
+// is applied by the evaluation pass (BlueIO::out_scaled).
+void adjoint_map(const CandSet& J, const LatticeDev& lat, int Luse, const uint64_t* umask, const BlueGeom& g,
+                 int32_t* map, double* inv_cnt, int64_t pairs, cudaStream_t s);
+void adjoint_bins(int Luse, int maxM, const BlueGeom& g, int64_t n, const int32_t* map, const double* inv_cnt,
+                  const cplx* coef, int64_t coef_stride, int nrhs, cplx* cs, cplx* bins, int64_t bins_stride,
+                  cudaStream_t s);
 
 // Planted sampler, lattice request: weights c_h e^{2 pi i h_(>t).x'} per
 // right-hand side (anchors [nrhs][d]) scattered to bin h_(1..t).z_l mod M_l.
