@@ -174,12 +174,12 @@ __global__ void __launch_bounds__(256) gather_kernel(CandSet J, LatticeDev lat, 
 #pragma unroll
       for (int i = 0; i < kGatherRhs; ++i)
         if (i < nh) y[i] = Ch[i * C_stride + o];
+      // acc += wo * y as four FMAs (FP64 instructions are the scarce resource)
 #pragma unroll
       for (int i = 0; i < kGatherRhs; ++i)
         if (i < nh) {
-          const cplx v = cmul(wo, y[i]);
-          acc[i].x += v.x;
-          acc[i].y += v.y;
+          acc[i].x = fma(wo.x, y[i].x, fma(-wo.y, y[i].y, acc[i].x));
+          acc[i].y = fma(wo.x, y[i].y, fma(wo.y, y[i].x, acc[i].y));
         }
     }
   }
