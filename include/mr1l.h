@@ -166,6 +166,12 @@ int mr1l_reconstruct(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* 
  *                 (the polynomial sum_k c_k e^{2 pi i k.x} at the nodes);
  *   MR1L_ADJOINT: y_{l,j} = sum_{k in I_l} c_k / (counter_k M_l) exp(2 pi i j k.z_l / M_l)
  *                 (the conjugate transpose of mr1l_reconstruct).
+ * Both are an inverse Bluestein transform of lattice bins.  EVAL sums the
+ * coefficients into bins k.z_l mod M_l with atomics (colliding frequencies
+ * share a bin).  ADJOINT writes every bin once from a bin -> frequency map
+ * that the plan builds on its first adjoint (sum_l M_l int32 and nI doubles
+ * of device memory, kept with the plan); its 1/M_l is applied after the
+ * transform.
  */
 int mr1l_evaluate(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode, void* stream);
 
