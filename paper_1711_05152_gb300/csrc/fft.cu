@@ -1468,21 +1468,6 @@ __global__ void noise_tables_kernel(NoiseTables* t) {
 
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }  // |e| <= 126
 
-// (double)x built from x's bits with integer operations only, for every
-// class of x (zero, subnormal, normal, infinite; a NaN stays a NaN).  The
-// conversion is exact, so the bits are the FP64 conversion's; the noise
-// kernel is bound by the FP64 pipe, where each conversion instruction costs
-// 16 SM cycles per warp on this GPU.
-__device__ __forceinline__ double f2d_int(float x) {
-  const uint32_t b = (uint32_t)__float_as_int(x);
-  const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-  const bool sub = e == 0u && m != 0u;
-  const int sh = sub ? __clz((int)m) - 8 : 0;                 // m << sh has bit 23 set
-  const uint32_t mm = sub ? ((m << sh) & 0x7fffffu) : m;
-  const uint32_t E = e == 0u ? (m == 0u ? 0u : 897u - (uint32_t)sh) : (e == 0xffu ? 2047u : e + 896u);
-  return __hiloint2double((int)((b & 0x80000000u) | (E << 20) | (mm >> 3)), (int)(mm << 29));
-}
-
 // ln(Q 2^-53) for Q in [1, 2^53] as a double-float (<= 0)
 __device__ __forceinline__ void ln_q53(uint64_t Q, const NoiseTables* T, float& lh, float& ll) {
   int e = 63 - __clzll((long long)Q);           // Q in [2^e, 2^(e+1))
@@ -1586,7 +1571,7 @@ __global__ void __launch_bounds__(256) lattice_noise_kernel(BlueGeom g, BlueIO i
   float reh, rel, imh, iml;
   dw_mul(Rh, Rl, cs.x, cs.y, reh, rel);
   dw_mul(Rh, Rl, sn.x, sn.y, imh, iml);
-  const cplx e = cmake(f2d_int(reh) + f2d_int(rel), f2d_int(imh) + f2d_int(iml));
+  const cplx e = cmake((double)reh + (double)rel, (double)imh + (double)iml);
   cplx* y = io.out + h * io.out_stride + g.off[l] + j;
   *y = io.noise_write ? e : cadd(*y, e);
 }
