@@ -170,8 +170,8 @@ int mr1l_reconstruct(mr1l_plan_t* plan, const void* y, int nrhs, void* c, void* 
  * coefficients into bins k.z_l mod M_l with atomics (colliding frequencies
  * share a bin).  ADJOINT writes every bin once from a bin -> frequency map
  * that the plan builds on its first adjoint (sum_l M_l int32 and nI doubles
- * of device memory, kept with the plan); its 1/M_l is applied after the
- * transform.
+ * of device memory, kept with the plan, plus nrhs x nI complex scratch for
+ * the scaled coefficients); its 1/M_l is applied after the transform.
  */
 int mr1l_evaluate(mr1l_plan_t* plan, const void* c, int nrhs, void* y, int mode, void* stream);
 
